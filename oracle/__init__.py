@@ -1,0 +1,184 @@
+"""FP64 CPU oracle of the GEM hot path (arXiv 2509.25075, Sec. 3.2 and the
+appendix derivation of the projection).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never calls it and shares no code with it.
+
+The arithmetic lives in ``gem_oracle.c`` (plain C, double precision, brute
+force); this module compiles it with gcc and wraps it with ctypes.  Inputs are
+converted to float64 here; outputs are float64 numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gem_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgem_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NPAR = 11
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available).  Returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:5] + ["-fopenmp"] + base[5:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I, L, D = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            sig = {
+                "gem_oracle_num_threads": (I, []),
+                "gem_oracle_preprocess": (None, [I, L, P, I, P, P, P]),
+                "gem_oracle_project": (None, [I, D, D, I, L, P, I, P, P, P]),
+                "gem_oracle_project_pixels": (None, [I, D, D, I, L, P, I, P, P, L, P, P]),
+                "gem_oracle_tile_hits": (None, [I, D, D, I, I, L, P, I, P, P, P]),
+                "gem_oracle_ctf_value": (D, [P, D, D]),
+                "gem_oracle_ctf_grid_from_params": (None, [I, D, I, P, P]),
+                "gem_oracle_ctf_grid_from_half": (None, [I, I, P, P]),
+                "gem_oracle_ctf_apply": (None, [I, I, P, P, P]),
+                "gem_oracle_loss": (D, [I, I, P, P, P, P, P, P]),
+                "gem_oracle_grad": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().gem_oracle_num_threads())
+
+
+def preprocess(params, R, t, norm_mode: int = 0) -> np.ndarray:
+    """Per (view, Gaussian): [mean x, mean y, cov xx, cov xy, cov yy, amp, depth, valid]."""
+    params, R, t = _f64(params), _f64(R), _f64(t)
+    M, B = params.shape[0], R.shape[0]
+    out = np.zeros((B, M, 8))
+    _load().gem_oracle_preprocess(norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(out))
+    return out
+
+
+def project(params, R, t, d: int, apix: float, tau: float, norm_mode: int = 0) -> np.ndarray:
+    """Eq. render with Eq. accu: [B][d][d] projections."""
+    params, R, t = _f64(params), _f64(R), _f64(t)
+    M, B = params.shape[0], R.shape[0]
+    img = np.zeros((B, d, d))
+    _load().gem_oracle_project(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(img))
+    return img
+
+
+def project_pixels(params, R, t, d, apix, tau, pix, norm_mode: int = 0) -> np.ndarray:
+    """Projection at selected flat pixel indices pix = (b*d + v)*d + u."""
+    params, R, t = _f64(params), _f64(R), _f64(t)
+    pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    out = np.zeros(pix.shape[0])
+    _load().gem_oracle_project_pixels(d, apix, tau, norm_mode, params.shape[0], _ptr(params), R.shape[0],
+                                      _ptr(R), _ptr(t), pix.shape[0], _ptr(pix), _ptr(out))
+    return out
+
+
+def tile_hits(params, R, t, d, apix, tau, tile, norm_mode: int = 0) -> np.ndarray:
+    """[B][M][T] uint8: some pixel centre of the tile has a value above tau."""
+    params, R, t = _f64(params), _f64(R), _f64(t)
+    M, B = params.shape[0], R.shape[0]
+    T = (d // tile) ** 2
+    out = np.zeros((B, M, T), dtype=np.uint8)
+    _load().gem_oracle_tile_hits(d, apix, tau, norm_mode, tile, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(out))
+    return out
+
+
+def ctf_value(prm, fx: float, fy: float) -> float:
+    prm = _f64(prm)
+    return float(_load().gem_oracle_ctf_value(_ptr(prm), float(fx), float(fy)))
+
+
+def ctf_grid_from_params(prm, d: int, apix: float) -> np.ndarray:
+    """[B][d][d] symmetrised transfer function from [B][8] CTF parameters."""
+    prm = _f64(prm)
+    B = prm.shape[0]
+    full = np.zeros((B, d, d))
+    _load().gem_oracle_ctf_grid_from_params(d, apix, B, _ptr(prm), _ptr(full))
+    return full
+
+
+def ctf_grid_from_half(half) -> np.ndarray:
+    """[B][d][d] symmetrised transfer function from a [B][d][d/2+1] array."""
+    half = _f64(half)
+    B, d = half.shape[0], half.shape[1]
+    full = np.zeros((B, d, d))
+    _load().gem_oracle_ctf_grid_from_half(d, B, _ptr(half), _ptr(full))
+    return full
+
+
+def ctf_apply(hfull, x) -> np.ndarray:
+    hfull, x = _f64(hfull), _f64(x)
+    B, d = x.shape[0], x.shape[1]
+    out = np.zeros_like(x)
+    _load().gem_oracle_ctf_apply(d, B, _ptr(hfull), _ptr(x), _ptr(out))
+    return out
+
+
+def loss(hfull, proj, images):
+    """Returns (L, pred, loss_img, g) of Eq. loss and its adjoint."""
+    hfull, proj, images = _f64(hfull), _f64(proj), _f64(images)
+    B, d = proj.shape[0], proj.shape[1]
+    pred = np.zeros_like(proj)
+    g = np.zeros_like(proj)
+    li = np.zeros(B)
+    L = _load().gem_oracle_loss(d, B, _ptr(hfull), _ptr(proj), _ptr(images), _ptr(pred), _ptr(li), _ptr(g))
+    return float(L), pred, li, g
+
+
+def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None) -> np.ndarray:
+    """dL/dtheta [nsel][11] given g = dL/dproj [B][d][d]."""
+    params, R, t, g = _f64(params), _f64(R), _f64(t), _f64(g)
+    M, B = params.shape[0], R.shape[0]
+    if sel is None:
+        nsel, selp, sel_arr = M, None, None
+    else:
+        sel_arr = np.ascontiguousarray(np.asarray(sel, dtype=np.int64))
+        nsel, selp = sel_arr.shape[0], _ptr(sel_arr)
+    out = np.zeros((nsel, NPAR))
+    _load().gem_oracle_grad(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(g),
+                            nsel, selp, _ptr(out))
+    return out
+
+
+def forward_loss(params, R, t, hfull, images, d, apix, tau, norm_mode: int = 0) -> float:
+    """L(theta) through the whole path; used for central differences."""
+    proj = project(params, R, t, d, apix, tau, norm_mode)
+    return loss(hfull, proj, images)[0]
