@@ -1,0 +1,391 @@
+"""Benchmark of the GEM hot path on GB300: particle images per second for one
+full step (projection a1-a3, CTF + loss + adjoint a4, sparse gradient a5-a6)
+on the synthetic stand-in for the paper's workloads.
+
+  python bench.py --gpus N --steps K --warmup W [--impl gem|reference]
+
+Prints one JSON line on rank 0.  Under torchrun every rank runs an
+independent replica on its own GPU (its own batch): the method's images are
+independent, so the step shards with no data-path collective ("weak"
+scaling); value = images of all ranks / the slowest rank's time.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the library's stream with an L2 flush (a 256 MB write) between steps,
+outside the events; barrier + synchronize on both sides of the timed region;
+max over ranks.  The ``e2e`` figure repeats the step through the public API
+with the step's inputs copied from pinned host memory and the loss and
+gradient copied back inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle images/s, forward + adjoint gradient (projection, CTF, L2 loss, sparse gradient) per GB300"
+UNIT = "images/s"
+# SFU (MUFU) base-2 exponentials per clock per SM on sm_103a, measured by an
+# in-bounds throughput probe; one exponential is the irreducible cost of a
+# kept (pixel, Gaussian) pair in both rasterisers.
+EX2_PER_CLK_PER_SM = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gem", "reference"], default="gem")
+    ap.add_argument("--workload", default="A2")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain dense form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def physical_gpu(local: int) -> str:
+    """nvidia-smi id of this rank's GPU (index or UUID)."""
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+    if cvd:
+        ids = [x.strip() for x in cvd.split(",") if x.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of x over the ranks of the default process group (x if none)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(images_per_rank: int, seconds_max: float, world: int) -> float:
+    """Whole-job images per second: every rank's images over the slowest rank's time."""
+    return images_per_rank * world / seconds_max
+
+
+# ------------------------------------------------------------ clocks -------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        # samples under load: the SM clock is above idle for a busy GPU
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None] or [0])}
+
+
+# ------------------------------------------------------------- oracle ------
+
+def oracle_sample(w, n_images: int, seed: int = 0):
+    """Time the FP64 oracle on n_images images of workload w (full M and d).
+    Returns (seconds, images, threads)."""
+    import oracle
+    from paper_2509_25075_gb300 import synthetic as syn
+
+    sub = syn.Workload(w.name, d=w.d, M=w.M, B=n_images, apix=w.apix, s_lo=w.s_lo, s_hi=w.s_hi,
+                       n_clusters=w.n_clusters, seed=w.seed)
+    inp = syn.batch(sub, seed=seed)
+    inp["params"] = syn.gaussians(w)  # the workload's own Gaussian set
+    t0 = time.perf_counter()
+    proj = oracle.project(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, w.norm_mode)
+    H = oracle.ctf_grid_from_params(inp["ctf_params"], w.d, w.apix)
+    _, _, _, g = oracle.loss(H, proj, inp["images"])
+    oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g, w.norm_mode)
+    dt = time.perf_counter() - t0
+    return dt, n_images, oracle.num_threads()
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    dt1, n1, thr = oracle_sample(w, 1)
+    n = max(1, min(16, int(budget_s / max(dt1, 1e-3))))
+    if n > 1:
+        dt, n, thr = oracle_sample(w, n, seed=1)
+    else:
+        dt, n = dt1, n1
+    return {"value": n / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{n} image(s) of workload {w.name} (d={w.d}, M={w.M}) through projection, "
+                      f"CTF + loss + adjoint and the full gradient, FP64 brute force, "
+                      f"{dt:.2f} s on {thr} host threads"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, K steps of a bounded sample."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2509_25075_gb300 import synthetic as syn
+
+    w = syn.WORKLOADS[args.workload]
+    for i in range(args.warmup):
+        oracle_sample(w, 1, seed=100 + i)
+    tot, imgs, thr = 0.0, 0, 1
+    for i in range(args.steps):
+        dt, n, thr = oracle_sample(w, 1, seed=200 + i)
+        tot += dt
+        imgs += n
+    value = imgs / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"1 image of workload {w.name} per step (full M and d), FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w):
+    return {"workload": f"{w.name}: GEM step on d={w.d} px images, M={w.M} Gaussians, B={w.B} images "
+                        f"per step, apix={w.apix} A, tau={w.tau:.4g}, scales {w.s_lo}-{w.s_hi} px, "
+                        f"{w.n_clusters} clusters, CTF from parameters",
+            "d": w.d, "M": w.M, "global_batch": w.B, "tau": w.tau, "norm_mode": w.norm_mode,
+            "zsort": 1, "l2": "flushed between timed steps (256 MB write)"}
+
+
+# --------------------------------------------------------------- main ------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_25075_gb300 import binding
+    from paper_2509_25075_gb300 import synthetic as syn
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = syn.WORKLOADS[args.workload]
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    host = syn.batch(w, seed=w.seed + 1000 * rank)
+    # the Gaussians are the model: the same on every rank
+    host["params"] = syn.gaussians(w)
+    D = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    ctx = binding.Context(w.d, w.apix, w.B, w.M, tau=w.tau, norm_mode=w.norm_mode, zsort=1, stream=stream)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(w.M, 11, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.gem_forward(D["params"], D["R"], D["t"], D["images"], loss, ctf_params=D["ctf_params"])
+        ctx.gem_backward(grad)
+
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    if ctx.gem_status() != 0:
+        raise RuntimeError("device status after warm-up: " + ctx.lib.gem_last_error(ctx.h).decode())
+
+    # ---- device-timed region ------------------------------------------------
+    ctx.gem_timing(True)
+    stage_ms = {k: 0.0 for k in binding.STAGES}
+    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(physical_gpu(local))
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        ms, ln = ctx.gem_timing_read()  # synchronises
+        for k in stage_ms:
+            stage_ms[k] += ms[k]
+        launches += sum(ln.values())
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.gem_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    status = ctx.gem_status()
+    if status != 0:
+        raise RuntimeError("device status after timed region: " + ctx.lib.gem_last_error(ctx.h).decode())
+    total_max = reduce_max(total_s, dev)
+    value = throughput(w.B * args.steps, total_max, ws)
+
+    # ---- end to end through the public API, host buffers ----------------------
+    pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in ("images", "R", "t", "ctf_params")}
+    out_grad = torch.empty(w.M, 11).pin_memory()
+    out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = out_grad.numel() * 4 + 8
+    e2e_steps = max(1, min(args.steps, 50))
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(e2e_steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        for k, v in pinned.items():
+            D[k].copy_(v, non_blocking=True)
+        step()
+        out_grad.copy_(grad, non_blocking=True)
+        out_loss.copy_(loss, non_blocking=True)
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e2e_s = reduce_max(sum(a.elapsed_time(b) for a, b in ee) / 1e3, dev)
+    e2e = {"value": throughput(w.B * e2e_steps, e2e_s, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    # ---- roofline of the dominant kernel ----------------------------------------
+    kept = ctx.gem_kept_pairs()
+    pairs = ctx.gem_pair_count()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    per_stage = {k: v / args.steps for k, v in stage_ms.items()}
+    dom = max(("raster_fwd", "raster_bwd"), key=lambda k: per_stage[k])
+    mhz = clk.get("sm_mhz") or 1455.0
+    peak = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # Gpair/s
+    achieved = kept / (per_stage[dom] / 1e3) / 1e9
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_note": f"{sms} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {mhz:.0f} MHz median SM clock "
+                         f"under load (one SFU exponential per kept pair)",
+            "kept_pairs_per_launch": kept, "listed_pairs_per_launch": pairs}
+
+    # ---- plain dense form -------------------------------------------------------
+    plain = None
+    if not args.no_plain:
+        pd = torch.empty(w.B, w.d, w.d, device=dev)
+        dp = torch.empty(w.B, w.d, w.d, device=dev)
+        g2 = torch.empty(w.M, 11, device=dev)
+
+        def pstep():
+            ctx.gem_project_dense(D["params"], D["R"], D["t"], pd)
+            ctx.gem_ctf_loss(pd, D["images"], ctf_params=D["ctf_params"], dproj=dp, loss=loss)
+            ctx.gem_project_backward_dense(dp, g2)
+
+        pstep()
+        torch.cuda.synchronize()
+        n_plain = 2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_plain):
+            pstep()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pv = w.B * n_plain / (a.elapsed_time(b) / 1e3)
+        plain = {"value": pv, "unit": UNIT, "speedup_of_tiled": value / ws / pv,
+                 "form": "one thread per pixel over all M Gaussians; one thread per (image, Gaussian) over all pixels"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": warm, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w), "clocks": clk, "e2e": e2e,
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "plain": plain,
+            "stages_ms": per_stage, "loss": float(loss.item()),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * gem.h -- C ABI of the GB300 (sm_103a) library for the GEM hot path.
+ *
+ * GEM (arXiv 2509.25075) writes a protein density as M anisotropic 3D
+ * Gaussians (11 values each, Sec. 3.2, Eq. G), projects them in closed form
+ * to particle images (Eq. render), keeps only terms above a threshold tau
+ * (Eq. accu), accumulates each pixel's terms from the lowest depth to the
+ * highest (Sec. 3.2, after Eq. accu), applies the CTF in Fourier space and
+ * scores the result with an L2 loss (Eq. loss), and back-propagates only
+ * through the (pixel, Gaussian) pairs that were kept (Sec. 1 (iii), Sec. 3.2
+ * "Efficient Gradient Computation").  Poses and CTFs are known inputs
+ * (Eq. recon).
+ *
+ * Conventions shared by every call
+ *   - Every array pointer is a DEVICE pointer owned by the caller, unless a
+ *     comment says otherwise.  The library never frees caller memory.  It
+ *     allocates its own scratch once, in gem_create, and frees it in
+ *     gem_destroy.
+ *   - Every call is asynchronous on the context's CUDA stream and does no
+ *     host synchronisation, except gem_status and gem_inspect_* (which
+ *     synchronise that stream).
+ *   - Return value: GEM_OK (0) or a negative GEM_E* code.  The message of
+ *     the last failure is available from gem_last_error.  A failed call
+ *     launches nothing.  No C++ exception crosses this interface.
+ *   - Device-side conditions (a list that overflowed its capacity) are
+ *     recorded in a status word that gem_status reads; they do not fault.
+ *   - Floating point is float32 (IEEE, row-major, contiguous) unless stated;
+ *     losses are float64.  Image arrays ([B][d][d]) must be 16-byte aligned.
+ *   - Image b, row v, column u is element [b][v][u] of a [B][d][d] array;
+ *     its centre sits at ((u - d/2) apix, (v - d/2) apix) Angstrom.
+ *   - Gaussian j is row j of a [M][11] array: p (3, Angstrom), s (3, the
+ *     diagonal of S in Eq. G, Angstrom), q (4, rotation quaternion w x y z,
+ *     normalised by the library), rho (1).  A Gaussian with a zero
+ *     quaternion, a non-positive rho, a singular projected covariance or a
+ *     non-finite value contributes nothing and receives a zero gradient.
+ *   - View b: R [B][3][3] row-major rotation, t [B][2] Angstrom; camera
+ *     coordinates are x' = R x + (t, 0) and the beam runs along z'.
+ *   - A context is not thread-safe; use one per stream.
+ */
+#ifndef GEM_H
+#define GEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEM_OK 0
+#define GEM_EINVAL (-1)    /* bad argument (null pointer, size out of range, bad config) */
+#define GEM_ENOMEM (-2)    /* device allocation failed in gem_create                      */
+#define GEM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed                 */
+#define GEM_ESTATE (-4)    /* call order violated (backward before forward, ...)          */
+#define GEM_ECAPACITY (-5) /* returned by gem_status: the pair list overflowed max_pairs  */
+
+/* Device status bits reported by gem_status. */
+#define GEM_STATUS_CAPACITY 1
+
+typedef struct gem_ctx gem_ctx;
+
+typedef struct gem_config {
+  int32_t d;         /* image side in pixels: a multiple of 16, 16..768, of the form 2^a 3^b  */
+  float apix;        /* pixel size in Angstrom, > 0                                          */
+  float tau;         /* threshold of Eq. accu on the 2D value, >= 0 (0: every pair counts)   */
+  int32_t norm_mode; /* 0: amplitude of Eq. render, rho / (2 pi |S^|^1/2) (rho is a mass);    */
+                     /* 1: exact line integral of Eq. G, rho (2 pi)^1/2 (|Sigma|/|S^|)^1/2    */
+  int32_t max_B;     /* largest batch any call will pass, >= 1                                */
+  int64_t max_M;     /* largest Gaussian count any call will pass, 1..2^24                    */
+  int64_t max_pairs; /* capacity of the (image, tile, Gaussian) lists; 0 picks 16*max_B*max_M */
+  int32_t zsort;     /* 1: accumulate each pixel from the lowest depth z' to the highest      */
+                     /*    (Sec. 3.2); 0: in Gaussian index order.  Changes rounding only.    */
+  int32_t reserved;  /* must be 0                                                             */
+} gem_config;
+
+/* Fill *cfg with defaults: tau = 0, norm_mode 0, zsort 1, max_pairs 0. */
+int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, int64_t max_M);
+
+/* Create a context.  cuda_stream is a cudaStream_t (NULL: the legacy default
+ * stream).  Allocates all scratch on the current device: about
+ * 32 B x max_B x max_M (projected records) + 24 B x max_B x max_M (moments)
+ * + 4 B x max_pairs x 1 (lists) + 20 B x max_B x d^2 (images, spectra) and
+ * a few small tables.  Errors: GEM_EINVAL, GEM_ENOMEM, GEM_ECUDA. */
+int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream);
+
+/* Message of the last gem_create that failed on this thread ("" after a success). */
+const char *gem_create_error(void);
+
+/* Free every allocation of the context (synchronises its stream).  NULL is allowed. */
+int gem_destroy(gem_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none); valid until the next call. */
+const char *gem_last_error(const gem_ctx *ctx);
+
+/* Change the stream later calls use. */
+int gem_set_stream(gem_ctx *ctx, void *cuda_stream);
+
+/* Synchronise the context's stream and return GEM_OK, GEM_ECAPACITY (the
+ * last projection needed more than max_pairs list entries; its outputs are
+ * incomplete) or GEM_ECUDA.  Clears the status word. */
+int gem_status(gem_ctx *ctx);
+
+/* ---- steps of the hot path -------------------------------------------- */
+
+/* Steps a1-a3: Eq. render with Eq. accu.
+ *   params [M][11], R [B][3][3], t [B][2]  ->  proj [B][d][d].
+ * Preprocesses every (view, Gaussian), bins the kept pairs into 16 x 16
+ * pixel tiles (each tile's Gaussians in ascending depth when zsort = 1) and
+ * rasterises.  The context keeps the bins and the pointers params, R, t for
+ * gem_project_backward: they must stay valid and unchanged until then.
+ * Errors: GEM_EINVAL (M < 1 or > max_M, B < 1 or > max_B, null pointer). */
+int gem_project(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
+                const float *t, float *proj);
+
+/* Step a4: Eq. loss and its adjoint, for B images.
+ *   proj [B][d][d], images [B][d][d], and exactly one of
+ *     ctf        [B][d][d/2+1]  real transfer function on the rfft grid
+ *                               [ky][kx]; where H(k) and H(-k mod d) differ
+ *                               (columns kx = 0 and d/2) their mean is used,
+ *     ctf_params [B][8]         defocus U (A), defocus V (A), astigmatism
+ *                               angle (rad), voltage (kV), Cs (mm), amplitude
+ *                               contrast, phase shift (rad), B-factor (A^2):
+ *                               H = -(sqrt(1-w^2) sin chi + w cos chi)
+ *                                   exp(-B k^2 / 4),
+ *                               chi = pi lambda dF(angle) k^2
+ *                                     - pi/2 Cs lambda^3 k^4 + phase.
+ *   pred    = F^-1(H . F(proj))              [B][d][d]   (may be NULL)
+ *   dproj   = dL/dproj = F^-1(H . F(2 r / (B d^2))), r = pred - images
+ *                                            [B][d][d]   (may be NULL)
+ *   loss_img[b] = (1/d^2) sum_pixels r^2     [B] float64 (may be NULL)
+ *   loss    = (1/B) sum_b loss_img[b]        [1] float64 (may be NULL)
+ * Circular convolution, no padding; forward DFT unnormalised, inverse 1/d^2.
+ * Errors: GEM_EINVAL (both or neither CTF form, B out of range, null input). */
+int gem_ctf_loss(gem_ctx *ctx, int32_t B, const float *proj, const float *ctf,
+                 const float *ctf_params, const float *images, float *pred, float *dproj,
+                 double *loss_img, double *loss);
+
+/* Steps a5-a6: gradient of the loss with respect to all 11 M parameters,
+ * given dproj = dL/dproj [B][d][d] for the projection of the last
+ * gem_project (same params, R, t, M, B).  Only the pairs kept by Eq. accu
+ * contribute.  grad [M][11] is overwritten.
+ * Errors: GEM_ESTATE (no projection yet), GEM_EINVAL. */
+int gem_project_backward(gem_ctx *ctx, const float *dproj, float *grad);
+
+/* a1-a4 in one call: gem_project into the context's own image buffer, then
+ * gem_ctf_loss with the adjoint kept inside the context for gem_backward.
+ * pred may be NULL; loss is a device float64 [1]. */
+int gem_forward(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
+                const float *t, const float *ctf, const float *ctf_params, const float *images,
+                float *pred, double *loss);
+
+/* a5-a6 for the last gem_forward: grad [M][11] = dL/dparams.
+ * Errors: GEM_ESTATE (no gem_forward since the last projection). */
+int gem_backward(gem_ctx *ctx, float *grad);
+
+/* ---- plain dense forms (no tiles, no binning, no ordering) -------------- */
+
+/* Same result as gem_project, computed by one thread per pixel over all M
+ * Gaussians.  Keeps the same state for gem_project_backward_dense. */
+int gem_project_dense(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
+                      const float *t, float *proj);
+
+/* Same result as gem_project_backward, computed by one thread per
+ * (view, Gaussian) over all d^2 pixels. */
+int gem_project_backward_dense(gem_ctx *ctx, const float *dproj, float *grad);
+
+/* ---- inspection (synchronise the stream) ------------------------------- */
+
+/* Number of (image, tile, Gaussian) entries the last gem_project listed. */
+int gem_pair_count(gem_ctx *ctx, int64_t *n_pairs);
+
+/* Copy the bins of the last gem_project into caller device memory:
+ *   tile_start [B*T + 1] int64: entries of tile t of image b are
+ *              list[tile_start[b*T + t] .. tile_start[b*T + t + 1]),
+ *              T = (d/16)^2, tiles numbered row-major;
+ *   list       [list_cap] uint32 Gaussian indices, in accumulation order.
+ * Errors: GEM_ESTATE, GEM_EINVAL (list_cap smaller than the pair count). */
+int gem_inspect_bins(gem_ctx *ctx, int64_t *tile_start, uint32_t *list, int64_t list_cap);
+
+/* Copy the projected records of the last gem_project, [B][M][8] float32:
+ * centre x, centre y (pixel coordinates: pixel u sits at x = u),
+ * conic xx, conic xy, conic yy (inverse projected covariance, pixel units),
+ * log2 of the 2D amplitude, depth z' (Angstrom), valid flag (1 or 0). */
+int gem_inspect_records(gem_ctx *ctx, float *out);
+
+/* Number of kept (pixel, Gaussian) pairs of the last gem_project (value > tau),
+ * counted by a separate pass over the bins.  Synchronises the stream. */
+int gem_kept_pairs(gem_ctx *ctx, int64_t *n_kept);
+
+/* ---- per-stage timing ---------------------------------------------------- */
+
+/* Stages of the hot path, as timed by gem_timing_read. */
+#define GEM_STAGE_PREP 0       /* a1: per-Gaussian and per-(view, Gaussian) preprocess   */
+#define GEM_STAGE_BIN 1        /* a2: depth sort and tile binning                         */
+#define GEM_STAGE_RASTER_FWD 2 /* a3: raster forward (or the dense forward)               */
+#define GEM_STAGE_CTF 3        /* a4: CTF, loss and adjoint                               */
+#define GEM_STAGE_RASTER_BWD 4 /* a5: moment clear + raster backward (or dense backward)  */
+#define GEM_STAGE_PREP_BWD 5   /* a6: chain rule to the 11 parameters, sum over views     */
+#define GEM_NSTAGES 6
+
+/* enable != 0: from now on record CUDA events on the context's stream around
+ * each stage and count the library's kernel launches per stage.  Resets the
+ * counters.  Timing does not change any result. */
+int gem_timing(gem_ctx *ctx, int enable);
+
+/* Synchronise the stream; write each stage's device time (ms, the last time
+ * it ran since the previous read; 0 if it did not run) to ms[GEM_NSTAGES]
+ * and the number of kernels the library launched per stage since the
+ * previous read to launches[GEM_NSTAGES] (either may be NULL).  Resets. */
+int gem_timing_read(gem_ctx *ctx, float *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEM_H */

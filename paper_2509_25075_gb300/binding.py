@@ -1,0 +1,288 @@
+"""Thin Python binding of the C ABI in include/gem.h.
+
+Functions carry the C names and only marshal arguments: they check shapes,
+dtypes, devices and contiguity of torch tensors and pass raw pointers to
+``libgem.so``.  Every step of the computation runs in the CUDA library; there
+is no CPU or PyTorch fallback.  If the library has not been built the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+GEM_OK = 0
+GEM_EINVAL = -1
+GEM_ENOMEM = -2
+GEM_ECUDA = -3
+GEM_ESTATE = -4
+GEM_ECAPACITY = -5
+NPAR = 11
+
+
+class GemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"gem error {code}: {msg}")
+        self.code = code
+
+
+class gem_config(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int32),
+        ("apix", ctypes.c_float),
+        ("tau", ctypes.c_float),
+        ("norm_mode", ctypes.c_int32),
+        ("max_B", ctypes.c_int32),
+        ("max_M", ctypes.c_int64),
+        ("max_pairs", ctypes.c_int64),
+        ("zsort", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+# name -> (restype, argtypes)
+_P, _I32, _I64, _F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+SIGNATURES = {
+    "gem_config_default": (ctypes.c_int, [ctypes.POINTER(gem_config), _I32, _F, _I32, _I64]),
+    "gem_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(gem_config), _P]),
+    "gem_destroy": (ctypes.c_int, [_P]),
+    "gem_last_error": (ctypes.c_char_p, [_P]),
+    "gem_create_error": (ctypes.c_char_p, []),
+    "gem_set_stream": (ctypes.c_int, [_P, _P]),
+    "gem_status": (ctypes.c_int, [_P]),
+    "gem_project": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "gem_ctf_loss": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gem_project_backward": (ctypes.c_int, [_P, _P, _P]),
+    "gem_forward": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "gem_backward": (ctypes.c_int, [_P, _P]),
+    "gem_project_dense": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "gem_project_backward_dense": (ctypes.c_int, [_P, _P, _P]),
+    "gem_pair_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "gem_inspect_bins": (ctypes.c_int, [_P, _P, _P, _I64]),
+    "gem_inspect_records": (ctypes.c_int, [_P, _P]),
+    "gem_kept_pairs": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "gem_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
+}
+
+STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgem.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libgem.so is missing: run __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _check(x, name, shape, dtype=torch.float32, optional=False):
+    if x is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+
+
+class Context:
+    """Owns one gem_ctx.  Methods mirror the C calls of the same name."""
+
+    def __init__(self, d: int, apix: float, max_B: int, max_M: int, tau: float = 0.0,
+                 norm_mode: int = 0, zsort: int = 1, max_pairs: int = 0, stream=None):
+        self.lib = load()
+        cfg = gem_config()
+        self.lib.gem_config_default(ctypes.byref(cfg), d, apix, max_B, max_M)
+        cfg.tau = tau
+        cfg.norm_mode = norm_mode
+        cfg.zsort = zsort
+        cfg.max_pairs = max_pairs
+        self.cfg = cfg
+        self.d, self.apix, self.max_B, self.max_M = d, apix, max_B, max_M
+        self.device = torch.cuda.current_device()
+        s = torch.cuda.current_stream() if stream is None else stream
+        self.stream = s
+        h = ctypes.c_void_p()
+        rc = self.lib.gem_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(s.cuda_stream))
+        if rc != GEM_OK:
+            raise GemError(rc, self.lib.gem_create_error().decode())
+        self.h = h
+        self.M = None
+        self.B = None
+
+    # -- plumbing ------------------------------------------------------------
+    def _rc(self, rc):
+        if rc != GEM_OK:
+            raise GemError(rc, self.lib.gem_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gem_set_stream(self, stream):
+        self.stream = stream
+        self._rc(self.lib.gem_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def gem_status(self):
+        return self.lib.gem_status(self.h)
+
+    def _views(self, params, R, t):
+        M = params.shape[0] if params.dim() == 2 else -1
+        B = R.shape[0] if R.dim() >= 1 else -1
+        _check(params, "params", (M, NPAR))
+        _check(R, "R", (B, 3, 3))
+        _check(t, "t", (B, 2))
+        return M, B
+
+    # -- steps -----------------------------------------------------------------
+    def gem_project(self, params, R, t, proj):
+        M, B = self._views(params, R, t)
+        _check(proj, "proj", (B, self.d, self.d))
+        self._rc(self.lib.gem_project(self.h, _ptr(params), M, B, _ptr(R), _ptr(t), _ptr(proj)))
+        self.M, self.B = M, B
+
+    def gem_project_dense(self, params, R, t, proj):
+        M, B = self._views(params, R, t)
+        _check(proj, "proj", (B, self.d, self.d))
+        self._rc(self.lib.gem_project_dense(self.h, _ptr(params), M, B, _ptr(R), _ptr(t), _ptr(proj)))
+        self.M, self.B = M, B
+
+    def gem_ctf_loss(self, proj, images, ctf=None, ctf_params=None, pred=None, dproj=None,
+                     loss_img=None, loss=None):
+        B, d = proj.shape[0], self.d
+        _check(proj, "proj", (B, d, d))
+        _check(images, "images", (B, d, d))
+        _check(ctf, "ctf", (B, d, d // 2 + 1), optional=True)
+        _check(ctf_params, "ctf_params", (B, 8), optional=True)
+        _check(pred, "pred", (B, d, d), optional=True)
+        _check(dproj, "dproj", (B, d, d), optional=True)
+        _check(loss_img, "loss_img", (B,), torch.float64, optional=True)
+        _check(loss, "loss", (1,), torch.float64, optional=True)
+        self._rc(self.lib.gem_ctf_loss(self.h, B, _ptr(proj), _ptr(ctf), _ptr(ctf_params),
+                                       _ptr(images), _ptr(pred), _ptr(dproj), _ptr(loss_img),
+                                       _ptr(loss)))
+
+    def gem_project_backward(self, dproj, grad):
+        _check(dproj, "dproj", (self.B, self.d, self.d))
+        _check(grad, "grad", (self.M, NPAR))
+        self._rc(self.lib.gem_project_backward(self.h, _ptr(dproj), _ptr(grad)))
+
+    def gem_project_backward_dense(self, dproj, grad):
+        _check(dproj, "dproj", (self.B, self.d, self.d))
+        _check(grad, "grad", (self.M, NPAR))
+        self._rc(self.lib.gem_project_backward_dense(self.h, _ptr(dproj), _ptr(grad)))
+
+    def gem_forward(self, params, R, t, images, loss, ctf=None, ctf_params=None, pred=None):
+        M, B = self._views(params, R, t)
+        d = self.d
+        _check(images, "images", (B, d, d))
+        _check(ctf, "ctf", (B, d, d // 2 + 1), optional=True)
+        _check(ctf_params, "ctf_params", (B, 8), optional=True)
+        _check(pred, "pred", (B, d, d), optional=True)
+        _check(loss, "loss", (1,), torch.float64)
+        self._rc(self.lib.gem_forward(self.h, _ptr(params), M, B, _ptr(R), _ptr(t), _ptr(ctf),
+                                      _ptr(ctf_params), _ptr(images), _ptr(pred), _ptr(loss)))
+        self.M, self.B = M, B
+
+    def gem_backward(self, grad):
+        _check(grad, "grad", (self.M, NPAR))
+        self._rc(self.lib.gem_backward(self.h, _ptr(grad)))
+
+    # -- inspection --------------------------------------------------------------
+    def gem_pair_count(self) -> int:
+        n = ctypes.c_int64()
+        self._rc(self.lib.gem_pair_count(self.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def gem_inspect_bins(self):
+        n = self.gem_pair_count()
+        T = (self.d // 16) ** 2
+        ts = torch.empty(self.B * T + 1, dtype=torch.int64, device="cuda")
+        lst = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        self._rc(self.lib.gem_inspect_bins(self.h, _ptr(ts), _ptr(lst), lst.numel()))
+        return ts, lst[:n]
+
+    def gem_kept_pairs(self) -> int:
+        n = ctypes.c_int64()
+        self._rc(self.lib.gem_kept_pairs(self.h, ctypes.byref(n)))
+        return int(n.value)
+
+    def gem_timing(self, enable: bool):
+        self._rc(self.lib.gem_timing(self.h, 1 if enable else 0))
+
+    def gem_timing_read(self):
+        """-> (ms per stage, kernel launches per stage), dicts keyed by STAGES."""
+        ms = (ctypes.c_float * len(STAGES))()
+        ln = (ctypes.c_int64 * len(STAGES))()
+        self._rc(self.lib.gem_timing_read(self.h, ctypes.cast(ms, ctypes.c_void_p),
+                                          ctypes.cast(ln, ctypes.c_void_p)))
+        return dict(zip(STAGES, list(ms))), dict(zip(STAGES, list(ln)))
+
+    def gem_inspect_records(self):
+        out = torch.empty(self.B, self.M, 8, dtype=torch.float32, device="cuda")
+        self._rc(self.lib.gem_inspect_records(self.h, _ptr(out)))
+        return out
+
+
+class GemLoss(torch.autograd.Function):
+    """loss = GemLoss.apply(params, R, t, ctf_params, images, ctx): forward a1-a4,
+    backward a5-a6 through the C library (poses, CTFs and images get no
+    gradient, as in Eq. recon where they are known)."""
+
+    @staticmethod
+    def forward(fctx, params, R, t, ctf_params, images, gctx):
+        loss = torch.empty(1, dtype=torch.float64, device=params.device)
+        gctx.gem_forward(params.detach().contiguous(), R, t, images, loss, ctf_params=ctf_params)
+        fctx.gctx = gctx
+        fctx.M = params.shape[0]
+        return loss[0]
+
+    @staticmethod
+    def backward(fctx, gout):
+        grad = torch.empty(fctx.M, NPAR, dtype=torch.float32, device=gout.device)
+        fctx.gctx.gem_backward(grad)
+        grad = grad * gout.to(grad.dtype)
+        return grad, None, None, None, None, None

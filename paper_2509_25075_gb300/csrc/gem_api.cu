@@ -1,0 +1,482 @@
+// C ABI of the GEM hot-path library (declared in include/gem.h).
+//
+// The context owns every scratch buffer (allocated once at creation, sized
+// by max_B, max_M, d and max_pairs) and records what the last projection
+// left behind for the backward pass.  Calls validate their arguments, then
+// enqueue kernels on the context's stream without synchronising.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "gem.h"
+#include "gem_internal.cuh"
+
+using namespace gem;
+
+struct gem_ctx {
+  gem_config cfg;
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+  int T = 0;
+  float l2tau = 0.f;
+  FftPlan plan{};
+  // scratch
+  GaussPrep *gp = nullptr;
+  Rec *rec = nullptr;
+  float *depth = nullptr;
+  BinScratch bin{};
+  float *mom = nullptr;
+  float *part = nullptr;
+  int nbg = 1;
+  float *proj = nullptr;   // internal projection of gem_forward
+  float *dproj = nullptr;  // internal adjoint of gem_forward
+  float2 *Z = nullptr;
+  float2 *tw = nullptr;
+  double *lossp = nullptr;
+  int *status = nullptr;
+  unsigned long long *kept = nullptr;
+  std::vector<void *> allocs;
+  // per-stage timing (events recorded around each stage when enabled)
+  bool timing = false;
+  cudaEvent_t ev[GEM_NSTAGES][2] = {};
+  bool recorded[GEM_NSTAGES] = {};
+  int64_t launches[GEM_NSTAGES] = {};
+  // state of the last projection
+  bool have_proj = false;
+  bool have_dproj = false;
+  const float *params = nullptr;
+  const float *R = nullptr;
+  const float *t = nullptr;
+  int64_t M = 0;
+  int B = 0;
+};
+
+static int fail(gem_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+static int cuda_fail(gem_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, GEM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Brackets one stage with events when timing is on and counts its kernels.
+struct StageScope {
+  gem_ctx *c;
+  int st;
+  StageScope(gem_ctx *c_, int st_, int kernels) : c(c_), st(st_) {
+    c->launches[st] += kernels;
+    if (c->timing) cudaEventRecord(c->ev[st][0], c->stream);
+  }
+  ~StageScope() {
+    if (c->timing) {
+      cudaEventRecord(c->ev[st][1], c->stream);
+      c->recorded[st] = true;
+    }
+  }
+};
+
+template <class T>
+static bool alloc(gem_ctx *c, T **p, size_t count) {
+  void *q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->allocs.push_back(q);
+  *p = (T *)q;
+  return true;
+}
+
+static bool d_ok(int d) {
+  if (d < 16 || d > 768 || d % 16 != 0) return false;
+  int m = d;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+static thread_local char g_create_err[512];
+
+extern "C" {
+
+const char *gem_create_error(void) { return g_create_err; }
+
+int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, int64_t max_M) {
+  if (!cfg) return GEM_EINVAL;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->d = d;
+  cfg->apix = apix;
+  cfg->tau = 0.f;
+  cfg->norm_mode = 0;
+  cfg->max_B = max_B;
+  cfg->max_M = max_M;
+  cfg->max_pairs = 0;
+  cfg->zsort = 1;
+  return GEM_OK;
+}
+
+int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
+  if (!out || !cfg) return GEM_EINVAL;
+  *out = nullptr;
+  gem_ctx *c = new (std::nothrow) gem_ctx();
+  if (!c) return GEM_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cuda_stream;
+  const gem_config &g = c->cfg;
+  int code = GEM_OK;
+  if (!d_ok(g.d))
+    code = fail(c, GEM_EINVAL, "d=%d: need a multiple of 16 in 16..768 of the form 2^a 3^b", g.d);
+  else if (!(g.apix > 0.f) || !isfinite(g.apix))
+    code = fail(c, GEM_EINVAL, "apix must be > 0");
+  else if (!(g.tau >= 0.f) || !isfinite(g.tau))
+    code = fail(c, GEM_EINVAL, "tau must be finite and >= 0");
+  else if (g.norm_mode != 0 && g.norm_mode != 1)
+    code = fail(c, GEM_EINVAL, "norm_mode must be 0 or 1");
+  else if (g.max_B < 1 || g.max_B > 65535)
+    code = fail(c, GEM_EINVAL, "max_B must be in 1..65535");
+  else if (g.max_M < 1 || g.max_M > (int64_t)1 << 24)
+    code = fail(c, GEM_EINVAL, "max_M must be in 1..2^24");
+  else if (g.max_pairs < 0)
+    code = fail(c, GEM_EINVAL, "max_pairs must be >= 0");
+  else if (g.zsort != 0 && g.zsort != 1)
+    code = fail(c, GEM_EINVAL, "zsort must be 0 or 1");
+  else if (g.reserved != 0)
+    code = fail(c, GEM_EINVAL, "reserved must be 0");
+  if (code != GEM_OK) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", c->err);
+    delete c;
+    return code;
+  }
+  if (c->cfg.max_pairs == 0) c->cfg.max_pairs = 16 * (int64_t)g.max_B * g.max_M;
+  const int d = g.d;
+  c->T = (d / kTile) * (d / kTile);
+  c->l2tau = g.tau > 0.f ? log2f(g.tau) : -INFINITY;
+  fft_plan(d, c->plan);
+  const size_t BM = (size_t)g.max_B * (size_t)g.max_M;
+  const size_t nchD = bin_chunks_depth(g.max_M), nchT = bin_chunks_tiles(g.max_M);
+  c->nbg = g.max_B < 16 ? g.max_B : 16;
+  bool ok = alloc(c, &c->gp, g.max_M) && alloc(c, &c->rec, BM) && alloc(c, &c->depth, BM) &&
+            alloc(c, &c->bin.keyA, BM) && alloc(c, &c->bin.keyB, BM) &&
+            alloc(c, &c->bin.valA, BM) && alloc(c, &c->bin.valB, BM) &&
+            alloc(c, &c->bin.dcnt, (size_t)g.max_B * nchD * 256) &&
+            alloc(c, &c->bin.tcnt, (size_t)g.max_B * nchT * c->T) &&
+            alloc(c, &c->bin.tile_start, (size_t)g.max_B * c->T + 1) &&
+            alloc(c, &c->bin.list, (size_t)c->cfg.max_pairs) && alloc(c, &c->mom, BM * 6) &&
+            alloc(c, &c->part, (size_t)c->nbg * g.max_M * kNpar) &&
+            alloc(c, &c->proj, (size_t)g.max_B * d * d) &&
+            alloc(c, &c->dproj, (size_t)g.max_B * d * d) &&
+            alloc(c, &c->Z, (size_t)g.max_B * d * d) && alloc(c, &c->tw, (size_t)d) &&
+            alloc(c, &c->lossp, (size_t)g.max_B * ctf_partials(d)) && alloc(c, &c->status, 1) &&
+            alloc(c, &c->kept, 1);
+  if (!ok) {
+    snprintf(g_create_err, sizeof(g_create_err), "device allocation failed");
+    gem_destroy(c);
+    return GEM_ENOMEM;
+  }
+  c->bin.cap = c->cfg.max_pairs;
+  c->bin.status = c->status;
+  std::vector<float2> tw(d);
+  for (int m = 0; m < d; ++m) {
+    double a = -2.0 * 3.14159265358979323846 * m / d;
+    tw[m] = make_float2((float)cos(a), (float)sin(a));
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpy(c->tw, tw.data(), d * sizeof(float2), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemset(c->status, 0, sizeof(int))) != cudaSuccess ||
+      (e = bin_configure(d)) != cudaSuccess || (e = ctf_configure(d)) != cudaSuccess) {
+    snprintf(g_create_err, sizeof(g_create_err), "set-up: %s", cudaGetErrorString(e));
+    gem_destroy(c);
+    return GEM_ECUDA;
+  }
+  g_create_err[0] = 0;
+  *out = c;
+  return GEM_OK;
+}
+
+int gem_destroy(gem_ctx *c) {
+  if (!c) return GEM_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (void *p : c->allocs) cudaFree(p);
+  for (int i = 0; i < GEM_NSTAGES; ++i)
+    for (int k = 0; k < 2; ++k)
+      if (c->ev[i][k]) cudaEventDestroy(c->ev[i][k]);
+  delete c;
+  return GEM_OK;
+}
+
+const char *gem_last_error(const gem_ctx *c) { return c ? c->err : ""; }
+
+int gem_set_stream(gem_ctx *c, void *s) {
+  if (!c) return GEM_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return GEM_OK;
+}
+
+int gem_status(gem_ctx *c) {
+  if (!c) return GEM_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+  int st = 0;
+  if ((e = cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "status read");
+  if ((e = cudaMemset(c->status, 0, sizeof(int))) != cudaSuccess)
+    return cuda_fail(c, e, "status clear");
+  if (st & GEM_STATUS_CAPACITY)
+    return fail(c, GEM_ECAPACITY, "pair list exceeded max_pairs=%lld",
+                (long long)c->cfg.max_pairs);
+  return GEM_OK;
+}
+
+static int check_project_args(gem_ctx *c, const float *params, int64_t M, int32_t B,
+                              const float *R, const float *t, const float *proj) {
+  if (!c) return GEM_EINVAL;
+  if (!params || !R || !t || !proj) return fail(c, GEM_EINVAL, "null pointer argument");
+  if (!aligned16(proj)) return fail(c, GEM_EINVAL, "proj must be 16-byte aligned");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  if (B < 1 || B > c->cfg.max_B)
+    return fail(c, GEM_EINVAL, "B=%d outside 1..max_B=%d", B, c->cfg.max_B);
+  return GEM_OK;
+}
+
+static int prep(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                const float *t) {
+  StageScope sc(c, GEM_STAGE_PREP, 2);
+  cudaError_t e;
+  const gem_config &g = c->cfg;
+  if ((e = launch_gauss_prep(params, M, g.norm_mode, c->gp, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "gauss_prep");
+  if ((e = launch_view_prep(c->gp, M, B, R, t, g.apix, g.d, c->l2tau, c->rec, c->depth,
+                            c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "view_prep");
+  c->params = params;
+  c->R = R;
+  c->t = t;
+  c->M = M;
+  c->B = B;
+  return GEM_OK;
+}
+
+int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                const float *t, float *proj) {
+  int rc = check_project_args(c, params, M, B, R, t, proj);
+  if (rc) return rc;
+  c->have_proj = false;
+  c->have_dproj = false;
+  if ((rc = prep(c, params, M, B, R, t))) return rc;
+  cudaError_t e;
+  const gem_config &g = c->cfg;
+  const uint32_t *perm = nullptr;
+  // depth keys span [-d apix, d apix]: the half-diagonal of the box is shorter
+  float zrange = (float)g.d * g.apix;
+  {
+    StageScope sc(c, GEM_STAGE_BIN, g.zsort ? 11 : 4);
+    if ((e = launch_bin(c->rec, c->depth, M, B, g.d, c->l2tau, zrange, g.zsort, c->bin, &perm,
+                        c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "bin");
+  }
+  {
+    StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
+    if ((e = launch_raster_fwd(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, M, B, g.d,
+                               c->l2tau, proj, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "raster_fwd");
+  }
+  c->have_proj = true;
+  return GEM_OK;
+}
+
+int gem_project_dense(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                      const float *t, float *proj) {
+  int rc = check_project_args(c, params, M, B, R, t, proj);
+  if (rc) return rc;
+  c->have_proj = false;
+  c->have_dproj = false;
+  if ((rc = prep(c, params, M, B, R, t))) return rc;
+  cudaError_t e;
+  StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
+  if ((e = launch_dense_fwd(c->rec, M, B, c->cfg.d, c->l2tau, proj, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "dense_fwd");
+  c->have_proj = true;
+  return GEM_OK;
+}
+
+int gem_ctf_loss(gem_ctx *c, int32_t B, const float *proj, const float *ctf,
+                 const float *ctf_params, const float *images, float *pred, float *dproj,
+                 double *loss_img, double *loss) {
+  if (!c) return GEM_EINVAL;
+  if (!proj || !images) return fail(c, GEM_EINVAL, "null proj or images");
+  if (!aligned16(proj) || !aligned16(images) || !aligned16(pred) || !aligned16(dproj))
+    return fail(c, GEM_EINVAL, "image arrays must be 16-byte aligned");
+  if ((ctf == nullptr) == (ctf_params == nullptr))
+    return fail(c, GEM_EINVAL, "pass exactly one of ctf and ctf_params");
+  if (B < 1 || B > c->cfg.max_B)
+    return fail(c, GEM_EINVAL, "B=%d outside 1..max_B=%d", B, c->cfg.max_B);
+  StageScope sc(c, GEM_STAGE_CTF, (loss_img || loss) ? 4 : 3);
+  cudaError_t e = launch_ctf_loss(c->cfg.d, B, c->cfg.apix, c->plan, c->tw, proj, ctf,
+                                  ctf_params, images, c->Z, c->lossp, pred, dproj, loss_img,
+                                  loss, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ctf_loss");
+  return GEM_OK;
+}
+
+static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool dense) {
+  if (!c) return GEM_EINVAL;
+  if (!dproj || !grad) return fail(c, GEM_EINVAL, "null dproj or grad");
+  if (!aligned16(dproj)) return fail(c, GEM_EINVAL, "dproj must be 16-byte aligned");
+  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection to differentiate");
+  const gem_config &g = c->cfg;
+  cudaError_t e;
+  size_t mbytes = (size_t)c->B * c->M * 6 * sizeof(float);
+  {
+    StageScope sc(c, GEM_STAGE_RASTER_BWD, 1);
+    if (!dense && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "moment clear");
+    if (dense)
+      e = launch_dense_bwd(c->rec, c->M, c->B, g.d, c->l2tau, dproj, c->mom, c->stream);
+    else
+      e = launch_raster_bwd(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, c->M, c->B,
+                            g.d, c->l2tau, dproj, c->mom, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
+  }
+  StageScope sc(c, GEM_STAGE_PREP_BWD, 2);
+  if ((e = launch_prep_bwd(c->params, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode,
+                           c->mom, c->part, c->nbg, grad, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "prep_bwd");
+  return GEM_OK;
+}
+
+int gem_project_backward(gem_ctx *c, const float *dproj, float *grad) {
+  return backward_common(c, dproj, grad, false);
+}
+
+int gem_project_backward_dense(gem_ctx *c, const float *dproj, float *grad) {
+  return backward_common(c, dproj, grad, true);
+}
+
+int gem_forward(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                const float *t, const float *ctf, const float *ctf_params, const float *images,
+                float *pred, double *loss) {
+  if (!c) return GEM_EINVAL;
+  if (!images) return fail(c, GEM_EINVAL, "null images");
+  if ((ctf == nullptr) == (ctf_params == nullptr))
+    return fail(c, GEM_EINVAL, "pass exactly one of ctf and ctf_params");
+  int rc = gem_project(c, params, M, B, R, t, c->proj);
+  if (rc) return rc;
+  rc = gem_ctf_loss(c, B, c->proj, ctf, ctf_params, images, pred, c->dproj, nullptr, loss);
+  if (rc) return rc;
+  c->have_dproj = true;
+  return GEM_OK;
+}
+
+int gem_backward(gem_ctx *c, float *grad) {
+  if (!c) return GEM_EINVAL;
+  if (!c->have_dproj) return fail(c, GEM_ESTATE, "gem_backward needs a gem_forward first");
+  return gem_project_backward(c, c->dproj, grad);
+}
+
+int gem_pair_count(gem_ctx *c, int64_t *n) {
+  if (!c || !n) return GEM_EINVAL;
+  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+  e = cudaMemcpy(n, c->bin.tile_start + (int64_t)c->B * c->T, sizeof(int64_t),
+                 cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair count read");
+  return GEM_OK;
+}
+
+int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t list_cap) {
+  if (!c || !tile_start || !list) return GEM_EINVAL;
+  int64_t n = 0;
+  int rc = gem_pair_count(c, &n);
+  if (rc) return rc;
+  if (n > c->bin.cap) return fail(c, GEM_ECAPACITY, "lists overflowed max_pairs");
+  if (list_cap < n) return fail(c, GEM_EINVAL, "list_cap %lld < pair count %lld",
+                                (long long)list_cap, (long long)n);
+  cudaError_t e;
+  size_t ts = ((size_t)c->B * c->T + 1) * sizeof(int64_t);
+  if ((e = cudaMemcpy(tile_start, c->bin.tile_start, ts, cudaMemcpyDeviceToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(list, c->bin.list, (size_t)n * sizeof(uint32_t),
+                      cudaMemcpyDeviceToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "inspect copy");
+  return GEM_OK;
+}
+
+int gem_inspect_records(gem_ctx *c, float *out) {
+  if (!c || !out) return GEM_EINVAL;
+  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
+  cudaError_t e = launch_inspect_records(c->rec, c->depth, c->M, c->B, out, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "inspect records");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "synchronise");
+  return GEM_OK;
+}
+
+int gem_kept_pairs(gem_ctx *c, int64_t *n) {
+  if (!c || !n) return GEM_EINVAL;
+  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
+  const gem_config &g = c->cfg;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c->kept, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess ||
+      (e = launch_count_kept(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, c->M, c->B,
+                             g.d, c->l2tau, c->kept, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "kept pair count");
+  unsigned long long h = 0;
+  if ((e = cudaMemcpy(&h, c->kept, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "kept pair read");
+  *n = (int64_t)h;
+  return GEM_OK;
+}
+
+int gem_timing(gem_ctx *c, int enable) {
+  if (!c) return GEM_EINVAL;
+  if (enable && !c->ev[0][0]) {
+    for (int i = 0; i < GEM_NSTAGES; ++i)
+      for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaEventCreate(&c->ev[i][k]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "event create");
+      }
+  }
+  c->timing = enable != 0;
+  for (int i = 0; i < GEM_NSTAGES; ++i) {
+    c->recorded[i] = false;
+    c->launches[i] = 0;
+  }
+  return GEM_OK;
+}
+
+int gem_timing_read(gem_ctx *c, float *ms, int64_t *launches) {
+  if (!c) return GEM_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+  for (int i = 0; i < GEM_NSTAGES; ++i) {
+    float t = 0.f;
+    if (c->recorded[i] && (e = cudaEventElapsedTime(&t, c->ev[i][0], c->ev[i][1])) != cudaSuccess)
+      return cuda_fail(c, e, "event elapsed");
+    if (ms) ms[i] = t;
+    if (launches) launches[i] = c->launches[i];
+    c->recorded[i] = false;
+    c->launches[i] = 0;
+  }
+  return GEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+// Step a4 of the GEM hot path: Eq. loss and its adjoint.
+//
+//   I_pred = F^-1(H . F(I^)),  r = I_pred - I,  L = (1/B) sum_b mean(r^2),
+//   dL/dI^ = F^-1(H . F(2 r / (B d^2)))   (H real and even: self-adjoint).
+//
+// Both real images of a view are packed into one complex image
+// z = I^ + i I, so F(z) = X + i Y with X = F(I^), Y = F(I) recovered from the
+// Hermitian symmetry of real spectra.  In Fourier space
+//   P = H X,  R = H X - Y  (= F(r)),  G = (2 / (B d^2)) H R,
+// the loss is (by Parseval) sum |R|^2 / d^4 per image, and one inverse
+// transform of W = P + i G returns I_pred (real part) and dL/dI^ (imaginary
+// part).  So each image costs one forward and one inverse complex 2D FFT.
+//
+// Three passes through a [B][d][d] complex buffer, stored transposed
+// (Z[b][kx][y]) so that every FFT runs on contiguous lines:
+//   pass 1: FFT along x of 16 rows of z, written transposed;
+//   pass 2: FFT along y of the lines kx and d - kx (8 pairs per CTA),
+//           CTF, loss, W, inverse FFT along y, written back in place;
+//   pass 3: inverse FFT along x of 16 rows, split into I_pred and dL/dI^.
+// FFTs are radix-4/2/3 Stockham transforms in shared memory (d = 2^a 3^b).
+#include <math.h>
+
+#include "gem_internal.cuh"
+
+namespace gem {
+
+bool fft_plan(int n, FftPlan &p) {
+  p.n = n;
+  p.nst = 0;
+  int m = n;
+  while (m % 3 == 0) {
+    p.radix[p.nst++] = 3;
+    m /= 3;
+  }
+  while (m % 4 == 0) {
+    p.radix[p.nst++] = 4;
+    m /= 4;
+  }
+  if (m % 2 == 0) {
+    p.radix[p.nst++] = 2;
+    m /= 2;
+  }
+  return m == 1 && p.nst <= 16;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Forward (e^{-2 pi i}) FFT of nl lines of length n, src -> dst -> src ...;
+// returns the buffer holding the result.  tw[m] = e^{-2 pi i m / n}.
+__device__ float2 *fft_lines(float2 *src, float2 *dst, int nl, const FftPlan &pl,
+                             const float2 *__restrict__ tw) {
+  const int n = pl.n;
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.radix[s];
+    const int nb = n / R;
+    const int tws = n / (Ns * R);
+    const int total = nl * nb;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int line = idx / nb;
+      const int jj = idx - line * nb;
+      const float2 *in = src + line * n;
+      float2 *out = dst + line * n;
+      const int k = jj % Ns;
+      float2 v[4];
+      for (int r = 0; r < R; ++r) v[r] = in[jj + r * nb];
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
+      if (R == 4) {
+        float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        float2 a2 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        float2 a3 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);  // (v1 - v3) * (-i)
+        v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
+        v[2] = make_float2(a0.x - a2.x, a0.y - a2.y);
+        v[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
+        v[3] = make_float2(a1.x - a3.x, a1.y - a3.y);
+      } else if (R == 2) {
+        float2 a0 = v[0];
+        v[0] = make_float2(a0.x + v[1].x, a0.y + v[1].y);
+        v[1] = make_float2(a0.x - v[1].x, a0.y - v[1].y);
+      } else {  // R == 3
+        const float h = 0.8660254037844386f;  // sqrt(3)/2
+        float2 t1 = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
+        float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+        float2 t3 = make_float2(h * (v[1].y - v[2].y), -h * (v[1].x - v[2].x));  // (v1-v2)(-i h)
+        v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
+        v[1] = make_float2(t2.x + t3.x, t2.y + t3.y);
+        v[2] = make_float2(t2.x - t3.x, t2.y - t3.y);
+      }
+      const int obase = (jj / Ns) * Ns * R + k;
+      for (int r = 0; r < R; ++r) out[obase + r * Ns] = v[r];
+    }
+    __syncthreads();
+    float2 *tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= R;
+  }
+  return src;
+}
+
+constexpr int kLines = 16;  // lines per CTA in every pass
+constexpr int kCtfThreads = 256;
+
+static size_t ctf_smem(int d) { return (size_t)(2 * kLines * d + d) * sizeof(float2); }
+
+__device__ __forceinline__ void load_twiddles(float2 *tw_s, const float2 *__restrict__ tw,
+                                              int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw_s[i] = tw[i];
+}
+
+// pass 1: rows y0..y0+15 of z = proj + i images -> FFT along x -> Z[b][kx][y]
+__global__ void __launch_bounds__(kCtfThreads) ctf_pass1_kernel(
+    const float *__restrict__ proj, const float *__restrict__ images, FftPlan pl,
+    const float2 *__restrict__ tw, float2 *__restrict__ Z) {
+  extern __shared__ float2 sm[];
+  const int d = pl.n;
+  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int y0 = blockIdx.x * kLines, b = blockIdx.y;
+  load_twiddles(tws, tw, d);
+  const float *pr = proj + ((int64_t)b * d + y0) * d;
+  const float *im = images + ((int64_t)b * d + y0) * d;
+  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) a[i] = make_float2(pr[i], im[i]);
+  __syncthreads();
+  float2 *res = fft_lines(a, bb, kLines, pl, tws);
+  float2 *zb = Z + (int64_t)b * d * d;
+  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
+    int l = i % kLines, kx = i / kLines;
+    zb[(int64_t)kx * d + y0 + l] = res[l * d + kx];
+  }
+}
+
+// Per-image CTF constants for the parameter form (see gem_ctf_value below).
+struct CtfConst {
+  float c1h, c1l;  // turns per n^2 of the mean-defocus term, split hi/lo
+  float c2, c3;    // astigmatic terms: turns per (kx^2 - ky^2) and per 2 kx ky
+  float c4;        // spherical aberration: turns per n^4
+  float ph;        // phase shift, turns
+  float sw, w;     // sqrt(1 - w^2), w
+  float bq;        // B-factor damping per n^2
+};
+
+__device__ CtfConst ctf_const(const float *__restrict__ prm, int d, float apix) {
+  // chi / (2 pi) = lambda/2 dF(angle) k^2 - Cs lambda^3 k^4 / 4 + phase / (2 pi),
+  // k = n / (d apix) for the signed bin indices n = (kx, ky).  dF(angle) k^2
+  // expands into integer multiples (kx^2 + ky^2, kx^2 - ky^2, 2 kx ky) of
+  // per-image constants, so no angle is formed.  The largest term (a few
+  // tens of turns at Nyquist) is split so that its high part times the
+  // integer n^2 is exact in float32 and can be reduced modulo one turn.
+  double dU = prm[0], dV = prm[1], ang = prm[2], volt = (double)prm[3] * 1e3;
+  double cs = (double)prm[4] * 1e7, w = prm[5], phase = prm[6], bf = prm[7];
+  double lam = 12.2643247 / sqrt(volt * (1.0 + 0.978466e-6 * volt));
+  double cf = 1.0 / ((double)d * apix * (double)d * apix);
+  double mean = 0.5 * (dU + dV), half = 0.5 * (dU - dV);
+  double c1 = 0.5 * lam * mean * cf;
+  CtfConst c;
+  int ex;
+  double mant = frexp(c1, &ex);            // c1 = mant * 2^ex, mant in [0.5, 1)
+  double hi = ldexp(floor(mant * 16.0) / 16.0, ex);  // 4 significant bits
+  c.c1h = (float)hi;
+  c.c1l = (float)(c1 - hi);
+  c.c2 = (float)(0.5 * lam * half * cos(2.0 * ang) * cf);
+  c.c3 = (float)(0.5 * lam * half * sin(2.0 * ang) * cf);
+  c.c4 = (float)(0.25 * cs * lam * lam * lam * cf * cf);
+  c.ph = (float)(phase / (2.0 * 3.14159265358979323846));
+  c.sw = (float)sqrt(1.0 - w * w);
+  c.w = (float)w;
+  c.bq = (float)(bf * cf / 4.0);
+  return c;
+}
+
+// CTF at signed bin indices (sx, sy).
+__device__ __forceinline__ float ctf_at(const CtfConst &c, int sx, int sy) {
+  float x2 = (float)(sx * sx), y2 = (float)(sy * sy);
+  float n2 = x2 + y2;                 // exact
+  float th = c.c1h * n2;              // exact
+  th -= rintf(th);
+  float turns = th + c.c1l * n2 + c.c2 * (x2 - y2) + c.c3 * (float)(2 * sx * sy) -
+                c.c4 * n2 * n2 + c.ph;
+  float s, co;
+  sincospif(2.f * turns, &s, &co);
+  return -(c.sw * s + c.w * co) * __expf(-c.bq * n2);
+}
+
+__device__ __forceinline__ int signed_bin(int k, int d) { return k < d / 2 ? k : k - d; }
+
+// pass 2: lines kx1 = 8 c + i (i < 8, kx1 <= d/2) and their partners
+// kx2 = (d - kx1) mod d.
+__global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
+    FftPlan pl, const float2 *__restrict__ tw, const float *__restrict__ ctf,
+    const float *__restrict__ ctf_params, float apix, float cscale, float2 *__restrict__ Z,
+    double *__restrict__ lossp, int nblk) {
+  extern __shared__ float2 sm[];
+  __shared__ CtfConst cc;
+  __shared__ double red[kCtfThreads / 32];
+  const int d = pl.n, hd = d / 2;
+  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int blk = blockIdx.x, b = blockIdx.y;
+  load_twiddles(tws, tw, d);
+  if (ctf_params && threadIdx.x == 0) cc = ctf_const(ctf_params + 8 * b, d, apix);
+  float2 *zb = Z + (int64_t)b * d * d;
+  // load the 16 lines: i < 8 -> kx1, i >= 8 -> kx2
+  for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
+    int i = idx / d, y = idx - i * d;
+    int kx1 = 8 * blk + (i & 7);
+    float2 v = make_float2(0.f, 0.f);
+    if (kx1 <= hd) {
+      int kx = i < 8 ? kx1 : (d - kx1) % d;
+      v = zb[(int64_t)kx * d + y];
+    }
+    a[idx] = v;
+  }
+  __syncthreads();
+  float2 *L = fft_lines(a, bb, kLines, pl, tws);
+  // combine: thread per (pair i, ky)
+  float lsum = 0.f;
+  for (int idx = threadIdx.x; idx < 8 * d; idx += blockDim.x) {
+    int i = idx / d, ky = idx - i * d;
+    int kx = 8 * blk + i;
+    if (kx > hd) continue;
+    bool self = (kx == 0 || kx == hd);
+    if (self && ky > hd) continue;
+    int mky = (d - ky) % d;
+    float2 *l1 = L + i * d;
+    float2 *l2 = self ? l1 : L + (8 + i) * d;
+    float2 z1 = l1[ky], z2 = l2[mky];
+    // X = (z1 + conj z2) / 2,  Y = (z1 - conj z2) / (2 i)
+    float2 X = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+    float2 Yv = make_float2(0.5f * (z1.y + z2.y), -0.5f * (z1.x - z2.x));
+    float h;
+    if (ctf_params) {
+      int sx = signed_bin(kx, d), sy = signed_bin(ky, d);
+      h = ctf_at(cc, sx, sy);
+      if (kx == hd || ky == hd) {
+        int px = signed_bin((d - kx) % d, d), py = signed_bin(mky, d);
+        h = 0.5f * (h + ctf_at(cc, px, py));
+      }
+    } else {
+      const float *hb = ctf + (int64_t)b * d * (hd + 1);
+      h = hb[(int64_t)ky * (hd + 1) + kx];
+      if (self) h = 0.5f * (h + hb[(int64_t)mky * (hd + 1) + kx]);
+    }
+    float2 P = make_float2(h * X.x, h * X.y);
+    float2 Rr = make_float2(P.x - Yv.x, P.y - Yv.y);
+    float2 G = make_float2(cscale * h * Rr.x, cscale * h * Rr.y);
+    float r2 = Rr.x * Rr.x + Rr.y * Rr.y;
+    bool lone = self && (ky == 0 || ky == hd);
+    lsum += lone ? r2 : 2.f * r2;
+    // W(k) = P + i G;  W(-k) = conj P + i conj G.  Stored conjugated: the
+    // inverse transform runs as conj(FFT(conj .)).
+    float2 W = make_float2(P.x - G.y, P.y + G.x);
+    float2 Wm = make_float2(P.x + G.y, -P.y + G.x);
+    l1[ky] = make_float2(W.x, -W.y);
+    l2[mky] = make_float2(Wm.x, -Wm.y);
+  }
+  // block reduction of the loss partial in float64
+  double ls = (double)lsum;
+  for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ls;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kCtfThreads / 32; ++w) s += red[w];
+    lossp[(int64_t)b * nblk + blk] = s;
+  }
+  // inverse along y (conjugated forward transform)
+  float2 *other = (L == a) ? bb : a;
+  float2 *R2 = fft_lines(L, other, kLines, pl, tws);
+  for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
+    int i = idx / d, y = idx - i * d;
+    int kx1 = 8 * blk + (i & 7);
+    if (kx1 > hd) continue;
+    bool self = (kx1 == 0 || kx1 == hd);
+    if (i >= 8 && self) continue;
+    int kx = i < 8 ? kx1 : d - kx1;
+    float2 v = R2[idx];
+    zb[(int64_t)kx * d + y] = make_float2(v.x, -v.y);
+  }
+}
+
+// pass 3: rows y0..y0+15 of W (read transposed) -> inverse FFT along x ->
+// I_pred = Re / d^2, dL/dI^ = Im / d^2.
+__global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
+    FftPlan pl, const float2 *__restrict__ tw, const float2 *__restrict__ Z, float inv_n2,
+    float *__restrict__ pred, float *__restrict__ dproj) {
+  extern __shared__ float2 sm[];
+  const int d = pl.n;
+  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int y0 = blockIdx.x * kLines, b = blockIdx.y;
+  load_twiddles(tws, tw, d);
+  const float2 *zb = Z + (int64_t)b * d * d;
+  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
+    int l = i % kLines, kx = i / kLines;
+    float2 v = zb[(int64_t)kx * d + y0 + l];
+    a[l * d + kx] = make_float2(v.x, -v.y);
+  }
+  __syncthreads();
+  float2 *res = fft_lines(a, bb, kLines, pl, tws);
+  int64_t off = ((int64_t)b * d + y0) * d;
+  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
+    float2 v = res[i];
+    if (pred) pred[off + i] = v.x * inv_n2;
+    if (dproj) dproj[off + i] = -v.y * inv_n2;
+  }
+}
+
+__global__ void loss_final_kernel(const double *__restrict__ lossp, int B, int nblk,
+                                  double inv_d4, double *__restrict__ loss_img,
+                                  double *__restrict__ loss) {
+  __shared__ double tot;
+  if (threadIdx.x == 0) tot = 0.0;
+  __syncthreads();
+  for (int b = 0; b < B; ++b) {
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int c = 0; c < nblk; ++c) s += lossp[(int64_t)b * nblk + c];
+      s *= inv_d4;
+      if (loss_img) loss_img[b] = s;
+      tot += s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) *loss = tot / B;
+}
+
+size_t ctf_partials(int d) { return (size_t)((d / 2 + 1 + 7) / 8); }
+
+cudaError_t ctf_configure(int d) {
+  int smem = (int)ctf_smem(d);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(ctf_pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(ctf_pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(ctf_pass3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
+}
+
+cudaError_t launch_ctf_loss(int d, int B, float apix, const FftPlan &plan, const float2 *tw,
+                            const float *proj, const float *ctf, const float *ctf_params,
+                            const float *images, float2 *Z, double *lossp, float *pred,
+                            float *dproj, double *loss_img, double *loss, cudaStream_t st) {
+  size_t smem = ctf_smem(d);
+  int nblk = (int)ctf_partials(d);
+  float cscale = (float)(2.0 / ((double)B * d * d));
+  ctf_pass1_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(proj, images, plan, tw, Z);
+  ctf_pass2_kernel<<<dim3(nblk, B), kCtfThreads, smem, st>>>(plan, tw, ctf, ctf_params, apix,
+                                                             cscale, Z, lossp, nblk);
+  ctf_pass3_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(
+      plan, tw, Z, (float)(1.0 / ((double)d * d)), pred, dproj);
+  if (loss_img || loss) {
+    double inv_d4 = 1.0 / ((double)d * d * (double)d * d);
+    loss_final_kernel<<<1, 32, 0, st>>>(lossp, B, nblk, inv_d4, loss_img, loss);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gem

@@ -1,0 +1,217 @@
+// Internal declarations of the GEM sm_103a library: record layout, device
+// helpers and the kernel launchers each .cu file provides to gem_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gem {
+
+constexpr int kTile = 16;     // tile side in pixels (Sec. 3.2 rasteriser, tiled)
+constexpr int kNpar = 11;     // parameters per Gaussian (Sec. 1, Sec. 3.2)
+constexpr float kLog2e = 1.4426950408889634f;
+// Margin, in log2 units of the exponent, by which tile lists and row ranges
+// are widened so that rounding in float32 never drops a pair whose value is
+// above tau; the per-pair test itself is exact (value > tau).
+constexpr float kMargin = 1e-3f;
+
+// Device status bits (mirror GEM_STATUS_* in gem.h).
+constexpr int kStatusCapacity = 1;
+
+// Per-Gaussian quantities independent of the view (48 B):
+//   p (3), Sigma (xx, xy, xz, yy, yz, zz), log2 of the amplitude constant,
+//   valid flag, padding.
+struct GaussPrep {
+  float p[3];
+  float sig[6];
+  float l2k;
+  float valid;
+  float pad;
+};
+
+// Projected record of one (view, Gaussian), 32 B, read by the binning and
+// the rasterisers as two float4:
+//   a = (px, py, ca, cb)  centre (pixel coordinates) and exponent terms
+//   b = (cc, l2A, rx, ry) exponent term, log2 amplitude, half extents
+// The base-2 exponent of the 2D value at pixel (u, v) is
+//   e = ca dx^2 + cb dx dy + cc dy^2 + l2A,  dx = u - px, dy = v - py,
+// so value = 2^e; the pair is kept when e > log2(tau).  rx, ry bound the
+// region where e > log2(tau) - margin.  A record whose amplitude cannot
+// exceed tau has rx = ry = -1 (no tile); an invalid record also has
+// l2A = -inf and ca = cb = cc = 0.
+struct __align__(16) Rec {
+  float4 a;
+  float4 b;
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Rotation matrix of a unit quaternion (w, x, y, z), entry formula.
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// The 2D Gaussian of one Gaussian in one view, in pixel units (Eq. render).
+// Both the forward preprocessing and the backward chain rule call this, so
+// the two sides see bit-identical quantities.
+struct View2D {
+  float px, py;          // centre, pixel coordinates
+  float sxx, sxy, syy;   // projected covariance S^, pixel^2
+  float cxx, cxy, cyy;   // conic S^^-1, 1/pixel^2
+  float l2A;             // log2 amplitude
+  float depth;           // z' (Angstrom)
+  bool valid;
+};
+
+__device__ __forceinline__ View2D view_project(const GaussPrep &g, const float *__restrict__ Rv,
+                                               const float *__restrict__ tv, float apix, int d) {
+  View2D o;
+  // mean: p' = R p + (t, 0)
+  float mx = Rv[0] * g.p[0] + Rv[1] * g.p[1] + Rv[2] * g.p[2] + tv[0];
+  float my = Rv[3] * g.p[0] + Rv[4] * g.p[1] + Rv[5] * g.p[2] + tv[1];
+  o.depth = Rv[6] * g.p[0] + Rv[7] * g.p[1] + Rv[8] * g.p[2];
+  float inv = 1.f / apix;
+  o.px = fmaf(mx, inv, 0.5f * d);
+  o.py = fmaf(my, inv, 0.5f * d);
+  // S^ = R2 Sigma R2^T, R2 = first two rows of R (Angstrom^2)
+  const float *s = g.sig;  // xx xy xz yy yz zz
+  float v0x = Rv[0] * s[0] + Rv[1] * s[1] + Rv[2] * s[2];
+  float v0y = Rv[0] * s[1] + Rv[1] * s[3] + Rv[2] * s[4];
+  float v0z = Rv[0] * s[2] + Rv[1] * s[4] + Rv[2] * s[5];
+  float v1x = Rv[3] * s[0] + Rv[4] * s[1] + Rv[5] * s[2];
+  float v1y = Rv[3] * s[1] + Rv[4] * s[3] + Rv[5] * s[4];
+  float v1z = Rv[3] * s[2] + Rv[4] * s[4] + Rv[5] * s[5];
+  float axx = v0x * Rv[0] + v0y * Rv[1] + v0z * Rv[2];
+  float axy = v0x * Rv[3] + v0y * Rv[4] + v0z * Rv[5];
+  float ayy = v1x * Rv[3] + v1y * Rv[4] + v1z * Rv[5];
+  float det = axx * ayy - axy * axy;  // Angstrom^4
+  float inv2 = inv * inv;
+  o.sxx = axx * inv2;
+  o.sxy = axy * inv2;
+  o.syy = ayy * inv2;
+  float detp = o.sxx * o.syy - o.sxy * o.sxy;
+  o.valid = g.valid != 0.f && det > 0.f && detp > 0.f && isfinite(det) && isfinite(o.px) &&
+            isfinite(o.py);
+  float idet = 1.f / detp;
+  o.cxx = o.syy * idet;
+  o.cyy = o.sxx * idet;
+  o.cxy = -o.sxy * idet;
+  o.l2A = g.l2k - 0.5f * log2f(det);
+  o.valid = o.valid && isfinite(o.l2A) && isfinite(o.cxx) && isfinite(o.cyy) && isfinite(o.cxy);
+  return o;
+}
+
+// Pixel range [lo, hi] covered by a centre c and half extent r inside
+// [0, d-1]; false if empty.
+__device__ __forceinline__ bool pixel_range(float c, float r, int d, int &lo, int &hi) {
+  if (!(r >= 0.f)) return false;
+  float l = fmaxf(ceilf(c - r), 0.f);
+  float h = fminf(floorf(c + r), (float)(d - 1));
+  if (!(l <= h)) return false;
+  lo = (int)l;
+  hi = (int)h;
+  return true;
+}
+
+// Does the region e > log2(tau) - margin of a record meet the tile
+// [x0, x0+15] x [y0, y0+15] of pixel centres?  Exact minimum of the
+// positive-definite quadratic Q = -(ca dx^2 + cb dx dy + cc dy^2) over the
+// rectangle, compared with kappa = l2A - log2(tau) + margin.
+__device__ __forceinline__ bool tile_hit(const Rec &r, int x0, int y0, float kappa) {
+  float al = -r.a.z, be = -r.a.w, ga = -r.b.x;
+  float ax = (float)x0 - r.a.x, bx = ax + (kTile - 1);
+  float ay = (float)y0 - r.a.y, by = ay + (kTile - 1);
+  if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
+  float best = INFINITY;
+  // edges dx = ax and dx = bx: minimise over dy in [ay, by]
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float dx = e ? bx : ax;
+    float dy = fminf(fmaxf(-be * dx / (2.f * ga), ay), by);
+    best = fminf(best, al * dx * dx + be * dx * dy + ga * dy * dy);
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    float dy = e ? by : ay;
+    float dx = fminf(fmaxf(-be * dy / (2.f * al), ax), bx);
+    best = fminf(best, al * dx * dx + be * dx * dy + ga * dy * dy);
+  }
+  return best <= kappa;
+}
+
+// ---- launchers (each returns cudaError_t of the launch) ------------------
+
+// gem_prep.cu
+cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, GaussPrep *gp,
+                              cudaStream_t st);
+cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
+                             const float *t, float apix, int d, float l2tau, Rec *rec,
+                             float *depth, cudaStream_t st);
+cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
+                            const float *R, const float *t, float apix, int d, int norm_mode,
+                            const float *mom, float *part, int nbg, float *grad,
+                            cudaStream_t st);
+cudaError_t launch_inspect_records(const Rec *rec, const float *depth, int64_t M, int B,
+                                   float *out, cudaStream_t st);
+
+// gem_bin.cu
+struct BinScratch {
+  uint16_t *keyA, *keyB;   // [B][M] depth keys
+  uint32_t *valA, *valB;   // [B][M] Gaussian indices
+  uint32_t *dcnt;          // [B][nchD][256]
+  uint32_t *tcnt;          // [B][nchT][T]
+  int64_t *tile_start;     // [B*T + 1]
+  uint32_t *list;          // [cap]
+  int64_t cap;
+  int *status;
+};
+// Returns the permutation used for binning in *perm_out (NULL: index order).
+cudaError_t launch_bin(const Rec *rec, const float *depth, int64_t M, int B, int d,
+                       float l2tau, float zrange, int zsort, BinScratch &s,
+                       const uint32_t **perm_out, cudaStream_t st);
+size_t bin_chunks_depth(int64_t M);
+size_t bin_chunks_tiles(int64_t M);
+cudaError_t bin_configure(int d);
+
+// gem_raster.cu
+cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
+                              int64_t cap, int64_t M, int B, int d, float l2tau, float *proj,
+                              cudaStream_t st);
+cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
+                              int64_t cap, int64_t M, int B, int d, float l2tau,
+                              const float *dproj, float *mom, cudaStream_t st);
+cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
+                              int64_t cap, int64_t M, int B, int d, float l2tau,
+                              unsigned long long *kept, cudaStream_t st);
+cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2tau, float *proj,
+                             cudaStream_t st);
+cudaError_t launch_dense_bwd(const Rec *rec, int64_t M, int B, int d, float l2tau,
+                             const float *dproj, float *mom, cudaStream_t st);
+
+// gem_ctf.cu
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[16];
+};
+bool fft_plan(int n, FftPlan &p);
+cudaError_t ctf_configure(int d);
+size_t ctf_partials(int d);
+cudaError_t launch_ctf_loss(int d, int B, float apix, const FftPlan &plan, const float2 *tw,
+                            const float *proj, const float *ctf, const float *ctf_params,
+                            const float *images, float2 *Z, double *lossp, float *pred,
+                            float *dproj, double *loss_img, double *loss, cudaStream_t st);
+
+}  // namespace gem

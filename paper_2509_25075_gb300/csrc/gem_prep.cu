@@ -1,0 +1,303 @@
+// Steps a1 (preprocess) and a6 (preprocess backward) of the GEM hot path.
+//
+// a1: per Gaussian, Sigma = R_q S S^T R_q^T (Eq. G, Sec. 3.2); per (view,
+//     Gaussian), the 2D Gaussian of Eq. render: centre, conic, amplitude and
+//     the extent of the region where it can exceed tau (Eq. accu).
+// a6: chain rule from the per-(view, Gaussian) moments accumulated by the
+//     raster backward to dL/d(p, s, q, rho), summed over the views.
+#include "gem_internal.cuh"
+
+namespace gem {
+
+// ---------------------------------------------------------------- a1 -----
+
+__global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict__ params,
+                                                         int64_t M, int norm_mode,
+                                                         GaussPrep *__restrict__ gp) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const float *th = params + j * kNpar;
+  float p0 = th[0], p1 = th[1], p2 = th[2];
+  float s0 = th[3], s1 = th[4], s2 = th[5];
+  float qw = th[6], qx = th[7], qy = th[8], qz = th[9];
+  float rho = th[10];
+  float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  bool ok = qn > 0.f && isfinite(qn) && rho > 0.f && isfinite(rho) && isfinite(s0) &&
+            isfinite(s1) && isfinite(s2) && isfinite(p0) && isfinite(p1) && isfinite(p2);
+  GaussPrep g;
+  g.p[0] = p0;
+  g.p[1] = p1;
+  g.p[2] = p2;
+  float iq = ok ? 1.f / qn : 0.f;
+  float R[9];
+  quat_rot(qw * iq, qx * iq, qy * iq, qz * iq, R);
+  float a0 = s0 * s0, a1 = s1 * s1, a2 = s2 * s2;
+  // Sigma = R diag(s^2) R^T
+  g.sig[0] = R[0] * R[0] * a0 + R[1] * R[1] * a1 + R[2] * R[2] * a2;
+  g.sig[1] = R[0] * R[3] * a0 + R[1] * R[4] * a1 + R[2] * R[5] * a2;
+  g.sig[2] = R[0] * R[6] * a0 + R[1] * R[7] * a1 + R[2] * R[8] * a2;
+  g.sig[3] = R[3] * R[3] * a0 + R[4] * R[4] * a1 + R[5] * R[5] * a2;
+  g.sig[4] = R[3] * R[6] * a0 + R[4] * R[7] * a1 + R[5] * R[8] * a2;
+  g.sig[5] = R[6] * R[6] * a0 + R[7] * R[7] * a1 + R[8] * R[8] * a2;
+  // amplitude constant: A = 2^l2k / sqrt(det S^ [Angstrom^4])
+  //   mode 0 (Eq. render):           2^l2k = rho / (2 pi)
+  //   mode 1 (line integral of G):   2^l2k = rho sqrt(2 pi) |s0 s1 s2|
+  const float two_pi = 6.283185307179586f;
+  if (norm_mode == 0)
+    g.l2k = log2f(rho / two_pi);
+  else
+    g.l2k = log2f(rho * sqrtf(two_pi) * fabsf(s0 * s1 * s2));
+  g.valid = (ok && isfinite(g.l2k)) ? 1.f : 0.f;
+  g.pad = 0.f;
+  gp[j] = g;
+}
+
+cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, GaussPrep *gp,
+                              cudaStream_t st) {
+  int blocks = (int)((M + 255) / 256);
+  gauss_prep_kernel<<<blocks, 256, 0, st>>>(params, M, norm_mode, gp);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restrict__ gp,
+                                                        int64_t M, const float *__restrict__ R,
+                                                        const float *__restrict__ t,
+                                                        float apix, int d, float l2tau,
+                                                        Rec *__restrict__ rec,
+                                                        float *__restrict__ depth) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (j >= M) return;
+  GaussPrep g = gp[j];
+  float Rl[9], tl[2];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);
+  tl[0] = __ldg(t + 2 * b);
+  tl[1] = __ldg(t + 2 * b + 1);
+  View2D v = view_project(g, Rl, tl, apix, d);
+  Rec r;
+  float kap = v.l2A - l2tau;  // exponent headroom above the threshold
+  if (v.valid) {
+    r.a = make_float4(v.px, v.py, -0.5f * kLog2e * v.cxx, -kLog2e * v.cxy);
+    r.b = make_float4(-0.5f * kLog2e * v.cyy, v.l2A, -1.f, -1.f);
+    if (kap > 0.f) {
+      // Q(d) = (log2 e / 2) d^T C d <= kappa + margin  =>
+      //   |dx| <= sqrt((kappa + margin) * Sxx * 2 / log2 e), same for y
+      float km = (kap + kMargin) * (2.f / kLog2e);
+      r.b.z = sqrtf(km * v.sxx);
+      r.b.w = sqrtf(km * v.syy);
+    }
+    // no headroom: no extent, so no tile; every per-pair test fails anyway
+  } else {
+    r.a = make_float4(v.px, v.py, 0.f, 0.f);
+    r.b = make_float4(0.f, -INFINITY, -1.f, -1.f);
+  }
+  rec[(int64_t)b * M + j] = r;
+  depth[(int64_t)b * M + j] = v.depth;
+}
+
+cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
+                             const float *t, float apix, int d, float l2tau, Rec *rec,
+                             float *depth, cudaStream_t st) {
+  dim3 grid((unsigned)((M + 255) / 256), (unsigned)B);
+  view_prep_kernel<<<grid, 256, 0, st>>>(gp, M, R, t, apix, d, l2tau, rec, depth);
+  return cudaGetLastError();
+}
+
+__global__ void inspect_records_kernel(const Rec *__restrict__ rec,
+                                       const float *__restrict__ depth, int64_t n,
+                                       float *__restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Rec r = rec[i];
+  float *o = out + i * 8;
+  bool valid = r.b.y > -INFINITY;
+  o[0] = r.a.x;
+  o[1] = r.a.y;
+  o[2] = r.a.z * (-2.f / kLog2e);
+  o[3] = r.a.w * (-1.f / kLog2e);
+  o[4] = r.b.x * (-2.f / kLog2e);
+  o[5] = r.b.y;
+  o[6] = depth[i];
+  o[7] = valid ? 1.f : 0.f;
+}
+
+cudaError_t launch_inspect_records(const Rec *rec, const float *depth, int64_t M, int B,
+                                   float *out, cudaStream_t st) {
+  int64_t n = M * B;
+  inspect_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, depth, n, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a6 -----
+
+// Compensated (Kahan) accumulation in float32.
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Moments of one (view, Gaussian), accumulated by the raster backward over
+// the kept pixels (pixel units, dx = u - px, dy = v - py, val = 2D value,
+// g = dL/dproj):
+//   m0 = sum g val,  m1 = sum g val dx,  m2 = sum g val dy,
+//   m3 = sum g val dx^2,  m4 = sum g val dx dy,  m5 = sum g val dy^2.
+// From them (C = conic, S^ = its inverse, both pixel units):
+//   dL/dpx, dL/dpy = C (m1, m2)
+//   dL/dC  (matrix form, dL = tr(G_C dC)) = -1/2 [[m3, m4], [m4, m5]]
+//   dL/dS^ = -C G_C C - 1/2 m0 C          (C = S^^-1 and A ~ |S^|^-1/2)
+//   dL/dSigma = R2^T dL/dS^ R2 / apix^2    (S^ = R2 Sigma R2^T / apix^2)
+//   dL/dp = R2^T (dL/dpx, dL/dpy) / apix
+//   dL/drho = m0 / rho;  mode 1 adds m0 / s_k to dL/ds_k.
+// The view-independent part (Sigma -> s, q) is applied once per thread to
+// the summed dL/dSigma.
+__global__ void __launch_bounds__(128) prep_bwd_kernel(
+    const float *__restrict__ params, const GaussPrep *__restrict__ gp, int64_t M, int B,
+    const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode,
+    const float *__restrict__ mom, int per_group, float *__restrict__ part) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int bg = blockIdx.y;
+  if (j >= M) return;
+  GaussPrep g = gp[j];
+  float *out = part + ((int64_t)bg * M + j) * kNpar;
+  if (g.valid == 0.f) {
+#pragma unroll
+    for (int m = 0; m < kNpar; ++m) out[m] = 0.f;
+    return;
+  }
+  Kahan GS[6], DP[3], M0;
+  float inv = 1.f / apix;
+  int b0 = bg * per_group, b1 = min(B, b0 + per_group);
+  for (int b = b0; b < b1; ++b) {
+    const float *mm = mom + ((int64_t)b * M + j) * 6;
+    float m0 = mm[0], m1 = mm[1], m2 = mm[2], m3 = mm[3], m4 = mm[4], m5 = mm[5];
+    if (m0 == 0.f && m1 == 0.f && m2 == 0.f && m3 == 0.f && m4 == 0.f && m5 == 0.f) continue;
+    float Rl[9], tl[2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);
+    tl[0] = __ldg(t + 2 * b);
+    tl[1] = __ldg(t + 2 * b + 1);
+    View2D v = view_project(g, Rl, tl, apix, d);
+    if (!v.valid) continue;
+    // d/dp^ (pixel units)
+    float gpx = v.cxx * m1 + v.cxy * m2;
+    float gpy = v.cxy * m1 + v.cyy * m2;
+    // G_C = -1/2 [[m3, m4], [m4, m5]];  T = C G_C C
+    float gxx = -0.5f * m3, gxy = -0.5f * m4, gyy = -0.5f * m5;
+    float u_xx = v.cxx * gxx + v.cxy * gxy, u_xy = v.cxx * gxy + v.cxy * gyy;
+    float u_yx = v.cxy * gxx + v.cyy * gxy, u_yy = v.cxy * gxy + v.cyy * gyy;
+    float t_xx = u_xx * v.cxx + u_xy * v.cxy;
+    float t_xy = u_xx * v.cxy + u_xy * v.cyy;
+    float t_yy = u_yx * v.cxy + u_yy * v.cyy;
+    // dL/dS^ (symmetric, matrix form)
+    float hxx = -t_xx - 0.5f * m0 * v.cxx;
+    float hxy = -t_xy - 0.5f * m0 * v.cxy;
+    float hyy = -t_yy - 0.5f * m0 * v.cyy;
+    // dL/dSigma = R2^T H R2 / apix^2
+    float i2 = inv * inv;
+    float r0[3] = {Rl[0], Rl[1], Rl[2]}, r1[3] = {Rl[3], Rl[4], Rl[5]};
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = a; c < 3; ++c) {
+        float val = r0[a] * (hxx * r0[c] + hxy * r1[c]) + r1[a] * (hxy * r0[c] + hyy * r1[c]);
+        GS[idx++].add(val * i2);
+      }
+    // dL/dp = R2^T (gpx, gpy) / apix
+#pragma unroll
+    for (int a = 0; a < 3; ++a) DP[a].add((r0[a] * gpx + r1[a] * gpy) * inv);
+    M0.add(m0);
+  }
+  // view-independent part: Sigma = Rq D Rq^T, D = diag(s^2)
+  const float *th = params + j * kNpar;
+  float s[3] = {th[3], th[4], th[5]};
+  float qw = th[6], qx = th[7], qy = th[8], qz = th[9], rho = th[10];
+  float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  float iq = 1.f / qn;
+  float w = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
+  float Rq[9];
+  quat_rot(w, x, y, z, Rq);
+  // symmetric G (3x3) from the 6 accumulated entries (xx xy xz yy yz zz);
+  // off-diagonal entries of the matrix gradient appear twice in tr(G dSigma)
+  float G[9];
+  G[0] = GS[0].s;
+  G[4] = GS[3].s;
+  G[8] = GS[5].s;
+  G[1] = G[3] = GS[1].s;
+  G[2] = G[6] = GS[2].s;
+  G[5] = G[7] = GS[4].s;
+  // K = G Rq ; dL/ds_k = 2 s_k (Rq^T G Rq)_kk ; dL/dRq = 2 G Rq D
+  float K[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      K[3 * a + c] = G[3 * a] * Rq[c] + G[3 * a + 1] * Rq[3 + c] + G[3 * a + 2] * Rq[6 + c];
+  float ds[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float dk = Rq[k] * K[k] + Rq[3 + k] * K[3 + k] + Rq[6 + k] * K[6 + k];
+    ds[k] = 2.f * s[k] * dk;
+    if (norm_mode != 0) ds[k] += M0.s / s[k];
+  }
+  float dR[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dR[3 * a + c] = 2.f * K[3 * a + c] * s[c] * s[c];
+  // derivatives of the entry formula of quat_rot with respect to (w, x, y, z)
+  float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] +
+                    z * dR[6] + w * dR[7] - 2.f * x * dR[8]);
+  float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] -
+                    w * dR[6] + z * dR[7] - 2.f * y * dR[8]);
+  float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
+                    y * dR[5] + x * dR[6] + y * dR[7]);
+  // through the normalisation q / |q|
+  float dot = w * dw + x * dx + y * dy + z * dz;
+  out[0] = DP[0].s;
+  out[1] = DP[1].s;
+  out[2] = DP[2].s;
+  out[3] = ds[0];
+  out[4] = ds[1];
+  out[5] = ds[2];
+  out[6] = (dw - w * dot) * iq;
+  out[7] = (dx - x * dot) * iq;
+  out[8] = (dy - y * dot) * iq;
+  out[9] = (dz - z * dot) * iq;
+  out[10] = M0.s / rho;
+}
+
+__global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__ part,
+                                                       int nbg, int64_t n,
+                                                       float *__restrict__ grad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Kahan acc;
+  for (int g = 0; g < nbg; ++g) acc.add(part[(int64_t)g * n + i]);
+  grad[i] = acc.s;
+}
+
+cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
+                            const float *R, const float *t, float apix, int d, int norm_mode,
+                            const float *mom, float *part, int nbg, float *grad,
+                            cudaStream_t st) {
+  int per = (B + nbg - 1) / nbg;
+  int groups = (B + per - 1) / per;
+  dim3 grid((unsigned)((M + 127) / 128), (unsigned)groups);
+  prep_bwd_kernel<<<grid, 128, 0, st>>>(params, gp, M, B, R, t, apix, d, norm_mode, mom, per,
+                                        part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t n = M * kNpar;
+  grad_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, groups, n, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace gem

@@ -1,0 +1,71 @@
+"""Shared helpers of the GPU tests: run a case on the GPU through the C ABI
+and on the oracle, and compare with the tolerances of the hot-path contract.
+
+Tolerances (float32 path against the FP64 oracle):
+  projection  max |dI| <= 1e-5 max |I| (+ tau for each pair whose value sits
+              within 1e-5 relative of tau, where float32 and float64 may take
+              the threshold decision differently)
+  loss        relative <= 1e-5
+  gradient    ||dg|| / ||g|| <= 1e-4, and per entry relative <= 1e-3 where
+              |g| > 1e-3 max |g|
+  pred, dL/dI max abs <= 1e-5 max |.|
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2509_25075_gb300 import binding
+from paper_2509_25075_gb300 import synthetic as syn
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(DEV)
+
+
+def inputs(w: syn.Workload, seed=None):
+    return syn.batch(w, seed=seed)
+
+
+def context(w: syn.Workload, **kw):
+    return binding.Context(w.d, w.apix, w.B, w.M, tau=kw.pop("tau", w.tau),
+                           norm_mode=kw.pop("norm_mode", w.norm_mode), **kw)
+
+
+def borderline_pairs(inp, w, tau, norm_mode=0, rel=1e-5):
+    """Number of (pixel, Gaussian) pairs whose FP64 value lies within
+    rel * tau of tau, per image (brute force, small cases only)."""
+    if tau <= 0:
+        return np.zeros(inp["R"].shape[0], dtype=np.int64)
+    B = inp["R"].shape[0]
+    M = inp["params"].shape[0]
+    counts = np.zeros(B, dtype=np.int64)
+    for j in range(M):
+        img = oracle.project(inp["params"][j:j + 1], inp["R"], inp["t"], w.d, w.apix, 0.0, norm_mode)
+        counts += np.sum(np.abs(img - tau) <= rel * tau, axis=(1, 2))
+    return counts
+
+
+def assert_proj_close(got, ref, tau=0.0, border=None, rel=1e-5):
+    got = np.asarray(got, dtype=np.float64)
+    scale = np.max(np.abs(ref))
+    allow = rel * scale
+    if border is not None:
+        allow = allow + tau * float(np.max(border))
+    err = np.max(np.abs(got - ref))
+    assert err <= allow, f"projection max err {err:.3e} > {allow:.3e} (scale {scale:.3e})"
+
+
+def assert_grad_close(got, ref, norm_tol=1e-4, entry_tol=1e-3):
+    got = np.asarray(got, dtype=np.float64)
+    nrm = np.linalg.norm(ref)
+    assert nrm > 0
+    rel = np.linalg.norm(got - ref) / nrm
+    assert rel <= norm_tol, f"gradient relative norm error {rel:.3e}"
+    big = np.abs(ref) > 1e-3 * np.max(np.abs(ref))
+    ent = np.max(np.abs(got[big] - ref[big]) / np.abs(ref[big]))
+    assert ent <= entry_tol, f"gradient per-entry relative error {ent:.3e}"
+    return rel, ent

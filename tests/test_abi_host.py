@@ -1,0 +1,74 @@
+"""Host-side checks that need no GPU: the library loads, exports every entry
+point include/gem.h declares, the binding covers them, and configuration
+errors are reported before any device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_25075_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gem_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["gem_create", "gem_destroy", "gem_project", "gem_ctf_loss", "gem_project_backward",
+              "gem_forward", "gem_backward", "gem_status", "gem_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build.build())
+    for n in _declared():
+        assert hasattr(lib, n), n
+    assert set(_declared()) <= set(binding.SIGNATURES), set(_declared()) - set(binding.SIGNATURES)
+
+
+def _create(**over):
+    lib = binding.load()
+    cfg = binding.gem_config()
+    assert lib.gem_config_default(ctypes.byref(cfg), 64, 1.2, 4, 100) == 0
+    assert (cfg.d, cfg.max_B, cfg.max_M, cfg.zsort, cfg.norm_mode) == (64, 4, 100, 1, 0)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p()
+    rc = lib.gem_create(ctypes.byref(h), ctypes.byref(cfg), None)
+    return rc, lib.gem_create_error().decode(), h
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("d", 40, "multiple of 16"),
+    ("d", 80, "2^a 3^b"),
+    ("d", 1024, "16..768"),
+    ("apix", 0.0, "apix"),
+    ("tau", -1.0, "tau"),
+    ("norm_mode", 2, "norm_mode"),
+    ("max_B", 0, "max_B"),
+    ("max_M", 0, "max_M"),
+    ("max_pairs", -5, "max_pairs"),
+    ("zsort", 3, "zsort"),
+    ("reserved", 1, "reserved"),
+])
+def test_bad_config_is_rejected_before_device_work(field, value, msg):
+    rc, err, h = _create(**{field: value})
+    assert rc == binding.GEM_EINVAL
+    assert msg in err
+    assert not h.value
+
+
+def test_null_arguments():
+    lib = binding.load()
+    assert lib.gem_create(None, None, None) == binding.GEM_EINVAL
+    assert lib.gem_destroy(None) == binding.GEM_OK
+    assert lib.gem_status(None) == binding.GEM_EINVAL
+    assert lib.gem_project(None, None, 1, 1, None, None, None) == binding.GEM_EINVAL
+    assert lib.gem_backward(None, None) == binding.GEM_EINVAL
+    assert lib.gem_last_error(None) == b""
