@@ -34,10 +34,12 @@ if ROOT not in sys.path:
 
 METRIC = "particle images/s, forward + adjoint gradient (projection, CTF, L2 loss, sparse gradient) per GB300"
 UNIT = "images/s"
-# SFU (MUFU) base-2 exponentials per clock per SM on sm_103a, measured by an
-# in-bounds throughput probe; one exponential is the irreducible cost of a
-# kept (pixel, Gaussian) pair in both rasterisers.
-EX2_PER_CLK_PER_SM = 16
+# SFU (MUFU) base-2 exponentials per clock per SM on sm_103a: 32, measured on
+# GB300 by a throughput probe (8 independent ex2.approx chains per thread, one
+# 1024-thread block per SM, clock64 span: 31.99 per clock per SM).  One
+# exponential is the irreducible cost of a kept (pixel, Gaussian) pair in
+# both rasterisers.
+EX2_PER_CLK_PER_SM = 32
 
 
 def parse():
@@ -327,7 +329,7 @@ def main():
            "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     # ---- roofline of the dominant kernel ----------------------------------------
-    kept = ctx.gem_kept_pairs()
+    kept, evaluated = ctx.gem_pair_stats()
     pairs = ctx.gem_pair_count()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -340,7 +342,8 @@ def main():
             "frac": achieved / peak, "traffic": None,
             "peak_note": f"{sms} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {mhz:.0f} MHz median SM clock "
                          f"under load (one SFU exponential per kept pair)",
-            "kept_pairs_per_launch": kept, "listed_pairs_per_launch": pairs}
+            "kept_pairs_per_launch": kept, "evaluated_pairs_per_launch": evaluated,
+            "listed_pairs_per_launch": pairs}
 
     # ---- plain dense form -------------------------------------------------------
     plain = None

@@ -182,9 +182,12 @@ int gem_inspect_bins(gem_ctx *ctx, int64_t *tile_start, uint32_t *list, int64_t 
  * log2 of the 2D amplitude, depth z' (Angstrom), valid flag (1 or 0). */
 int gem_inspect_records(gem_ctx *ctx, float *out);
 
-/* Number of kept (pixel, Gaussian) pairs of the last gem_project (value > tau),
- * counted by a separate pass over the bins.  Synchronises the stream. */
-int gem_kept_pairs(gem_ctx *ctx, int64_t *n_kept);
+/* Pair statistics of the last gem_project, counted by a separate pass over
+ * the bins (not part of the hot path; synchronises the stream):
+ *   kept      (pixel, Gaussian) pairs with value > tau (Eq. accu),
+ *   evaluated pairs the tiled forward rasteriser evaluates to find them
+ *             (may be NULL). */
+int gem_pair_stats(gem_ctx *ctx, int64_t *kept, int64_t *evaluated);
 
 /* ---- per-stage timing ---------------------------------------------------- */
 

@@ -68,7 +68,7 @@ SIGNATURES = {
     "gem_pair_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "gem_inspect_bins": (ctypes.c_int, [_P, _P, _P, _I64]),
     "gem_inspect_records": (ctypes.c_int, [_P, _P]),
-    "gem_kept_pairs": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "gem_pair_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "gem_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
 }
@@ -245,10 +245,11 @@ class Context:
         self._rc(self.lib.gem_inspect_bins(self.h, _ptr(ts), _ptr(lst), lst.numel()))
         return ts, lst[:n]
 
-    def gem_kept_pairs(self) -> int:
-        n = ctypes.c_int64()
-        self._rc(self.lib.gem_kept_pairs(self.h, ctypes.byref(n)))
-        return int(n.value)
+    def gem_pair_stats(self):
+        """-> (kept pairs, evaluated pairs) of the last projection."""
+        k, e = ctypes.c_int64(), ctypes.c_int64()
+        self._rc(self.lib.gem_pair_stats(self.h, ctypes.byref(k), ctypes.byref(e)))
+        return int(k.value), int(e.value)
 
     def gem_timing(self, enable: bool):
         self._rc(self.lib.gem_timing(self.h, 1 if enable else 0))

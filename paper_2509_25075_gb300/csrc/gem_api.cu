@@ -179,8 +179,8 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->proj, (size_t)g.max_B * d * d) &&
             alloc(c, &c->dproj, (size_t)g.max_B * d * d) &&
             alloc(c, &c->Z, (size_t)g.max_B * d * d) && alloc(c, &c->tw, (size_t)d) &&
-            alloc(c, &c->lossp, (size_t)g.max_B * ctf_partials(d)) && alloc(c, &c->status, 1) &&
-            alloc(c, &c->kept, 1);
+            alloc(c, &c->lossp, (size_t)g.max_B * (ctf_partials(d) + 1)) && alloc(c, &c->status, 1) &&
+            alloc(c, &c->kept, 2);
   if (!ok) {
     snprintf(g_create_err, sizeof(g_create_err), "device allocation failed");
     gem_destroy(c);
@@ -327,7 +327,7 @@ int gem_ctf_loss(gem_ctx *c, int32_t B, const float *proj, const float *ctf,
     return fail(c, GEM_EINVAL, "pass exactly one of ctf and ctf_params");
   if (B < 1 || B > c->cfg.max_B)
     return fail(c, GEM_EINVAL, "B=%d outside 1..max_B=%d", B, c->cfg.max_B);
-  StageScope sc(c, GEM_STAGE_CTF, (loss_img || loss) ? 4 : 3);
+  StageScope sc(c, GEM_STAGE_CTF, 3 + (loss_img || loss ? 1 : 0) + (loss ? 1 : 0));
   cudaError_t e = launch_ctf_loss(c->cfg.d, B, c->cfg.apix, c->plan, c->tw, proj, ctf,
                                   ctf_params, images, c->Z, c->lossp, pred, dproj, loss_img,
                                   loss, c->stream);
@@ -429,20 +429,22 @@ int gem_inspect_records(gem_ctx *c, float *out) {
   return GEM_OK;
 }
 
-int gem_kept_pairs(gem_ctx *c, int64_t *n) {
-  if (!c || !n) return GEM_EINVAL;
+int gem_pair_stats(gem_ctx *c, int64_t *kept, int64_t *evaluated) {
+  if (!c || !kept) return GEM_EINVAL;
   if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
   const gem_config &g = c->cfg;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(c->kept, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess ||
+  if ((e = cudaMemsetAsync(c->kept, 0, 2 * sizeof(unsigned long long), c->stream)) !=
+          cudaSuccess ||
       (e = launch_count_kept(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, c->M, c->B,
                              g.d, c->l2tau, c->kept, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
-    return cuda_fail(c, e, "kept pair count");
-  unsigned long long h = 0;
-  if ((e = cudaMemcpy(&h, c->kept, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(c, e, "kept pair read");
-  *n = (int64_t)h;
+    return cuda_fail(c, e, "pair count");
+  unsigned long long h[2] = {0, 0};
+  if ((e = cudaMemcpy(h, c->kept, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "pair count read");
+  *kept = (int64_t)h[0];
+  if (evaluated) *evaluated = (int64_t)h[1];
   return GEM_OK;
 }
 

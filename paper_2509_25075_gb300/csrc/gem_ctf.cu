@@ -6,10 +6,12 @@
 // Both real images of a view are packed into one complex image
 // z = I^ + i I, so F(z) = X + i Y with X = F(I^), Y = F(I) recovered from the
 // Hermitian symmetry of real spectra.  In Fourier space
-//   P = H X,  R = H X - Y  (= F(r)),  G = (2 / (B d^2)) H R,
+//   P = H X,  R = H X - Y  (= F(r)),  G = H R,
 // the loss is (by Parseval) sum |R|^2 / d^4 per image, and one inverse
-// transform of W = P + i G returns I_pred (real part) and dL/dI^ (imaginary
-// part).  So each image costs one forward and one inverse complex 2D FFT.
+// transform of W = P + i G returns I_pred (real part) and, times
+// 2 / (B d^2), dL/dI^ (imaginary part).  G is transformed unscaled so that
+// both halves of W have comparable magnitude and share the FFT's rounding
+// fairly.  So each image costs one forward and one inverse complex 2D FFT.
 //
 // Three passes through a [B][d][d] complex buffer, stored transposed
 // (Z[b][kx][y]) so that every FFT runs on contiguous lines:
@@ -27,24 +29,77 @@ namespace gem {
 bool fft_plan(int n, FftPlan &p) {
   p.n = n;
   p.nst = 0;
+  p.code = 0;
   int m = n;
-  while (m % 3 == 0) {
-    p.radix[p.nst++] = 3;
+  auto push = [&](unsigned c) {
+    p.code |= c << (2 * p.nst);
+    ++p.nst;
+  };
+  while (m % 3 == 0 && p.nst < 16) {
+    push(1);
     m /= 3;
   }
-  while (m % 4 == 0) {
-    p.radix[p.nst++] = 4;
+  while (m % 4 == 0 && p.nst < 16) {
+    push(2);
     m /= 4;
   }
-  if (m % 2 == 0) {
-    p.radix[p.nst++] = 2;
+  if (m % 2 == 0 && p.nst < 16) {
+    push(0);
     m /= 2;
   }
-  return m == 1 && p.nst <= 16;
+  return m == 1;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One radix-R Stockham stage on every line (kLines lines of length n).
+// Butterfly jj of a line reads elements jj + r n/R, twiddles them by
+// W^(r k n/(Ns R)), k = jj mod Ns, and writes (jj / Ns) Ns R + k + r Ns.
+template <int R>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ src, float2 *__restrict__ dst,
+                                          int nl, int n, int Ns, const float2 *__restrict__ tw) {
+  const int nb = n / R;
+  const int tws = n / (Ns * R);
+  const int total = nl * nb;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int line = idx / nb;
+    const int jj = idx - line * nb;
+    const float2 *in = src + line * n;
+    float2 *out = dst + line * n;
+    const int k = jj % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[jj + r * nb];
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
+    if (R == 4) {
+      float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+      float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+      float2 a2 = make_float2(v[1].x + v[3 % R].x, v[1].y + v[3 % R].y);
+      float2 a3 = make_float2(v[1].y - v[3 % R].y, v[3 % R].x - v[1].x);  // (v1 - v3) (-i)
+      v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
+      v[2 % R] = make_float2(a0.x - a2.x, a0.y - a2.y);
+      v[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
+      v[3 % R] = make_float2(a1.x - a3.x, a1.y - a3.y);
+    } else if (R == 2) {
+      float2 a0 = v[0];
+      v[0] = make_float2(a0.x + v[1].x, a0.y + v[1].y);
+      v[1] = make_float2(a0.x - v[1].x, a0.y - v[1].y);
+    } else {  // R == 3
+      const float h = 0.8660254037844386f;  // sqrt(3)/2
+      float2 t1 = make_float2(v[1].x + v[2 % R].x, v[1].y + v[2 % R].y);
+      float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+      float2 t3 = make_float2(h * (v[1].y - v[2 % R].y), -h * (v[1].x - v[2 % R].x));
+      v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
+      v[1] = make_float2(t2.x + t3.x, t2.y + t3.y);
+      v[2 % R] = make_float2(t2.x - t3.x, t2.y - t3.y);
+    }
+    const int obase = (jj / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[obase + r * Ns] = v[r];
+  }
 }
 
 // Forward (e^{-2 pi i}) FFT of nl lines of length n, src -> dst -> src ...;
@@ -54,44 +109,14 @@ __device__ float2 *fft_lines(float2 *src, float2 *dst, int nl, const FftPlan &pl
   const int n = pl.n;
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
-    const int R = pl.radix[s];
-    const int nb = n / R;
-    const int tws = n / (Ns * R);
-    const int total = nl * nb;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int line = idx / nb;
-      const int jj = idx - line * nb;
-      const float2 *in = src + line * n;
-      float2 *out = dst + line * n;
-      const int k = jj % Ns;
-      float2 v[4];
-      for (int r = 0; r < R; ++r) v[r] = in[jj + r * nb];
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
-      if (R == 4) {
-        float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-        float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-        float2 a2 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-        float2 a3 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);  // (v1 - v3) * (-i)
-        v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
-        v[2] = make_float2(a0.x - a2.x, a0.y - a2.y);
-        v[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
-        v[3] = make_float2(a1.x - a3.x, a1.y - a3.y);
-      } else if (R == 2) {
-        float2 a0 = v[0];
-        v[0] = make_float2(a0.x + v[1].x, a0.y + v[1].y);
-        v[1] = make_float2(a0.x - v[1].x, a0.y - v[1].y);
-      } else {  // R == 3
-        const float h = 0.8660254037844386f;  // sqrt(3)/2
-        float2 t1 = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
-        float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
-        float2 t3 = make_float2(h * (v[1].y - v[2].y), -h * (v[1].x - v[2].x));  // (v1-v2)(-i h)
-        v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
-        v[1] = make_float2(t2.x + t3.x, t2.y + t3.y);
-        v[2] = make_float2(t2.x - t3.x, t2.y - t3.y);
-      }
-      const int obase = (jj / Ns) * Ns * R + k;
-      for (int r = 0; r < R; ++r) out[obase + r * Ns] = v[r];
-    }
+    const unsigned c = (pl.code >> (2 * s)) & 3u;
+    const int R = c == 2 ? 4 : (c == 1 ? 3 : 2);
+    if (R == 4)
+      fft_stage<4>(src, dst, nl, n, Ns, tw);
+    else if (R == 2)
+      fft_stage<2>(src, dst, nl, n, Ns, tw);
+    else
+      fft_stage<3>(src, dst, nl, n, Ns, tw);
     __syncthreads();
     float2 *tmp = src;
     src = dst;
@@ -132,39 +157,69 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass1_kernel(
   }
 }
 
-// Per-image CTF constants for the parameter form (see gem_ctf_value below).
+// A float-float number hi + lo (|lo| <= ulp(hi) / 2).
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_split(double x) {
+  FF r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+
+// c * N for an integer-valued float N (|N| < 2^24), reduced modulo 1: the
+// product of the high parts is error-free (fmaf), its integer part dropped.
+__device__ __forceinline__ FF ff_mul_mod1(FF c, float N) {
+  float p = c.hi * N;
+  float e = fmaf(c.hi, N, -p);
+  FF r;
+  r.hi = p - rintf(p);
+  r.lo = fmaf(c.lo, N, e);
+  return r;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float err = (a.hi - (s - bb)) + (b.hi - bb);
+  FF r;
+  r.hi = s;
+  r.lo = err + a.lo + b.lo;
+  return r;
+}
+
+// Per-image CTF constants for the parameter form, in turns (chi / 2 pi):
+//   chi / (2 pi) = lambda/2 dF(angle) k^2 - Cs lambda^3 k^4 / 4 + phase / (2 pi),
+// with k = n / (d apix) for the signed bin indices n = (kx, ky).
+// dF(angle) k^2 expands into integer multiples (kx^2 + ky^2, kx^2 - ky^2,
+// 2 kx ky) of per-image constants, so no angle is formed, and every term is
+// a constant times an integer, evaluated in float-float and reduced modulo
+// one turn (tens of turns at Nyquist would otherwise cost float32 its
+// accuracy).
 struct CtfConst {
-  float c1h, c1l;  // turns per n^2 of the mean-defocus term, split hi/lo
-  float c2, c3;    // astigmatic terms: turns per (kx^2 - ky^2) and per 2 kx ky
-  float c4;        // spherical aberration: turns per n^4
-  float ph;        // phase shift, turns
-  float sw, w;     // sqrt(1 - w^2), w
-  float bq;        // B-factor damping per n^2
+  FF c1;   // turns per (kx^2 + ky^2), mean defocus
+  FF c2;   // turns per (kx^2 - ky^2), astigmatism
+  FF c3;   // turns per 2 kx ky, astigmatism
+  FF c4;   // turns per (kx^2 + ky^2)^2, spherical aberration
+  FF ph;   // phase shift, turns
+  float sw, w;  // sqrt(1 - w^2), w
+  float bq;     // B-factor damping per (kx^2 + ky^2)
 };
 
 __device__ CtfConst ctf_const(const float *__restrict__ prm, int d, float apix) {
-  // chi / (2 pi) = lambda/2 dF(angle) k^2 - Cs lambda^3 k^4 / 4 + phase / (2 pi),
-  // k = n / (d apix) for the signed bin indices n = (kx, ky).  dF(angle) k^2
-  // expands into integer multiples (kx^2 + ky^2, kx^2 - ky^2, 2 kx ky) of
-  // per-image constants, so no angle is formed.  The largest term (a few
-  // tens of turns at Nyquist) is split so that its high part times the
-  // integer n^2 is exact in float32 and can be reduced modulo one turn.
   double dU = prm[0], dV = prm[1], ang = prm[2], volt = (double)prm[3] * 1e3;
   double cs = (double)prm[4] * 1e7, w = prm[5], phase = prm[6], bf = prm[7];
   double lam = 12.2643247 / sqrt(volt * (1.0 + 0.978466e-6 * volt));
   double cf = 1.0 / ((double)d * apix * (double)d * apix);
   double mean = 0.5 * (dU + dV), half = 0.5 * (dU - dV);
-  double c1 = 0.5 * lam * mean * cf;
   CtfConst c;
-  int ex;
-  double mant = frexp(c1, &ex);            // c1 = mant * 2^ex, mant in [0.5, 1)
-  double hi = ldexp(floor(mant * 16.0) / 16.0, ex);  // 4 significant bits
-  c.c1h = (float)hi;
-  c.c1l = (float)(c1 - hi);
-  c.c2 = (float)(0.5 * lam * half * cos(2.0 * ang) * cf);
-  c.c3 = (float)(0.5 * lam * half * sin(2.0 * ang) * cf);
-  c.c4 = (float)(0.25 * cs * lam * lam * lam * cf * cf);
-  c.ph = (float)(phase / (2.0 * 3.14159265358979323846));
+  c.c1 = ff_split(0.5 * lam * mean * cf);
+  c.c2 = ff_split(0.5 * lam * half * cos(2.0 * ang) * cf);
+  c.c3 = ff_split(0.5 * lam * half * sin(2.0 * ang) * cf);
+  c.c4 = ff_split(-0.25 * cs * lam * lam * lam * cf * cf);
+  c.ph = ff_split(phase / (2.0 * 3.14159265358979323846));
   c.sw = (float)sqrt(1.0 - w * w);
   c.w = (float)w;
   c.bq = (float)(bf * cf / 4.0);
@@ -174,11 +229,18 @@ __device__ CtfConst ctf_const(const float *__restrict__ prm, int d, float apix) 
 // CTF at signed bin indices (sx, sy).
 __device__ __forceinline__ float ctf_at(const CtfConst &c, int sx, int sy) {
   float x2 = (float)(sx * sx), y2 = (float)(sy * sy);
-  float n2 = x2 + y2;                 // exact
-  float th = c.c1h * n2;              // exact
-  th -= rintf(th);
-  float turns = th + c.c1l * n2 + c.c2 * (x2 - y2) + c.c3 * (float)(2 * sx * sy) -
-                c.c4 * n2 * n2 + c.ph;
+  float n2 = x2 + y2;  // exact (< 2^24)
+  FF t = ff_mul_mod1(c.c1, n2);
+  t = ff_add(t, ff_mul_mod1(c.c2, x2 - y2));
+  t = ff_add(t, ff_mul_mod1(c.c3, (float)(2 * sx * sy)));
+  // (n2)^2 as an exact float-float q + qe, then c4 q mod 1 + c4 qe
+  float q = n2 * n2;
+  float qe = fmaf(n2, n2, -q);
+  FF t4 = ff_mul_mod1(c.c4, q);
+  t4.lo = fmaf(c.c4.hi, qe, t4.lo);
+  t = ff_add(t, t4);
+  t = ff_add(t, c.ph);
+  float turns = (t.hi - rintf(t.hi)) + t.lo;
   float s, co;
   sincospif(2.f * turns, &s, &co);
   return -(c.sw * s + c.w * co) * __expf(-c.bq * n2);
@@ -190,7 +252,7 @@ __device__ __forceinline__ int signed_bin(int k, int d) { return k < d / 2 ? k :
 // kx2 = (d - kx1) mod d.
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     FftPlan pl, const float2 *__restrict__ tw, const float *__restrict__ ctf,
-    const float *__restrict__ ctf_params, float apix, float cscale, float2 *__restrict__ Z,
+    const float *__restrict__ ctf_params, float apix, float2 *__restrict__ Z,
     double *__restrict__ lossp, int nblk) {
   extern __shared__ float2 sm[];
   __shared__ CtfConst cc;
@@ -244,7 +306,7 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     }
     float2 P = make_float2(h * X.x, h * X.y);
     float2 Rr = make_float2(P.x - Yv.x, P.y - Yv.y);
-    float2 G = make_float2(cscale * h * Rr.x, cscale * h * Rr.y);
+    float2 G = make_float2(h * Rr.x, h * Rr.y);
     float r2 = Rr.x * Rr.x + Rr.y * Rr.y;
     bool lone = self && (ky == 0 || ky == hd);
     lsum += lone ? r2 : 2.f * r2;
@@ -281,10 +343,10 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
 }
 
 // pass 3: rows y0..y0+15 of W (read transposed) -> inverse FFT along x ->
-// I_pred = Re / d^2, dL/dI^ = Im / d^2.
+// I_pred = Re / d^2, dL/dI^ = Im (2 / (B d^2)) / d^2.
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
     FftPlan pl, const float2 *__restrict__ tw, const float2 *__restrict__ Z, float inv_n2,
-    float *__restrict__ pred, float *__restrict__ dproj) {
+    float gscale, float *__restrict__ pred, float *__restrict__ dproj) {
   extern __shared__ float2 sm[];
   const int d = pl.n;
   float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
@@ -302,27 +364,36 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
     float2 v = res[i];
     if (pred) pred[off + i] = v.x * inv_n2;
-    if (dproj) dproj[off + i] = -v.y * inv_n2;
+    if (dproj) dproj[off + i] = -v.y * gscale;
   }
 }
 
-__global__ void loss_final_kernel(const double *__restrict__ lossp, int B, int nblk,
-                                  double inv_d4, double *__restrict__ loss_img,
-                                  double *__restrict__ loss) {
-  __shared__ double tot;
-  if (threadIdx.x == 0) tot = 0.0;
+// loss_img[b] = sum of image b's partials / d^4 (one warp per image, fixed
+// order: deterministic); loss = mean over images (one block, fixed order).
+__global__ void __launch_bounds__(256) loss_img_kernel(const double *__restrict__ lossp, int B,
+                                                       int nblk, double inv_d4,
+                                                       double *__restrict__ loss_img) {
+  int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int c = lane; c < nblk; c += 32) s += lossp[(int64_t)b * nblk + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) loss_img[b] = s * inv_d4;
+}
+
+__global__ void __launch_bounds__(256) loss_mean_kernel(const double *__restrict__ loss_img,
+                                                        int B, double *__restrict__ loss) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += loss_img[b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int b = 0; b < B; ++b) {
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int c = 0; c < nblk; ++c) s += lossp[(int64_t)b * nblk + c];
-      s *= inv_d4;
-      if (loss_img) loss_img[b] = s;
-      tot += s;
-    }
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    *loss = t / B;
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && loss) *loss = tot / B;
 }
 
 size_t ctf_partials(int d) { return (size_t)((d / 2 + 1 + 7) / 8); }
@@ -348,13 +419,18 @@ cudaError_t launch_ctf_loss(int d, int B, float apix, const FftPlan &plan, const
   int nblk = (int)ctf_partials(d);
   float cscale = (float)(2.0 / ((double)B * d * d));
   ctf_pass1_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(proj, images, plan, tw, Z);
-  ctf_pass2_kernel<<<dim3(nblk, B), kCtfThreads, smem, st>>>(plan, tw, ctf, ctf_params, apix,
-                                                             cscale, Z, lossp, nblk);
+  ctf_pass2_kernel<<<dim3(nblk, B), kCtfThreads, smem, st>>>(plan, tw, ctf, ctf_params, apix, Z,
+                                                             lossp, nblk);
   ctf_pass3_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(
-      plan, tw, Z, (float)(1.0 / ((double)d * d)), pred, dproj);
+      plan, tw, Z, (float)(1.0 / ((double)d * d)), (float)(cscale / ((double)d * d)), pred,
+      dproj);
   if (loss_img || loss) {
+    // per-image losses land in loss_img, or after the partials when the
+    // caller does not want them (lossp holds max_B * nblk + max_B doubles)
+    double *li = loss_img ? loss_img : lossp + (int64_t)B * nblk;
     double inv_d4 = 1.0 / ((double)d * d * (double)d * d);
-    loss_final_kernel<<<1, 32, 0, st>>>(lossp, B, nblk, inv_d4, loss_img, loss);
+    loss_img_kernel<<<(B + 7) / 8, 256, 0, st>>>(lossp, B, nblk, inv_d4, li);
+    if (loss) loss_mean_kernel<<<1, 256, 0, st>>>(li, B, loss);
   }
   return cudaGetLastError();
 }

@@ -125,14 +125,16 @@ __device__ __forceinline__ bool pixel_range(float c, float r, int d, int &lo, in
   return true;
 }
 
-// Does the region e > log2(tau) - margin of a record meet the tile
-// [x0, x0+15] x [y0, y0+15] of pixel centres?  Exact minimum of the
+// Does the region e > log2(tau) - margin of a record meet the rectangle
+// [x0, x0+side-1] x [y0, y0+side-1] of pixel centres?  Exact minimum of the
 // positive-definite quadratic Q = -(ca dx^2 + cb dx dy + cc dy^2) over the
 // rectangle, compared with kappa = l2A - log2(tau) + margin.
-__device__ __forceinline__ bool tile_hit(const Rec &r, int x0, int y0, float kappa) {
+__device__ __forceinline__ bool rect_hit(const Rec &r, int x0, int y0, int side, float kappa) {
   float al = -r.a.z, be = -r.a.w, ga = -r.b.x;
-  float ax = (float)x0 - r.a.x, bx = ax + (kTile - 1);
-  float ay = (float)y0 - r.a.y, by = ay + (kTile - 1);
+  float ax = (float)x0 - r.a.x, bx = ax + (float)(side - 1);
+  float ay = (float)y0 - r.a.y, by = ay + (float)(side - 1);
+  // outside the extent box: no need for the exact test
+  if (ax > r.b.z || bx < -r.b.z || ay > r.b.w || by < -r.b.w) return false;
   if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
   float best = INFINITY;
   // edges dx = ax and dx = bx: minimise over dy in [ay, by]
@@ -149,6 +151,20 @@ __device__ __forceinline__ bool tile_hit(const Rec &r, int x0, int y0, float kap
     best = fminf(best, al * dx * dx + be * dx * dy + ga * dy * dy);
   }
   return best <= kappa;
+}
+
+__device__ __forceinline__ bool tile_hit(const Rec &r, int x0, int y0, float kappa) {
+  return rect_hit(r, x0, y0, kTile, kappa);
+}
+
+// Bit q (q = 2 qy + qx) set when the record can exceed tau inside the 8x8
+// quadrant (qx, qy) of the tile whose top-left pixel is (x0, y0).
+__device__ __forceinline__ unsigned quadrant_mask(const Rec &r, int x0, int y0, float kappa) {
+  unsigned m = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (rect_hit(r, x0 + 8 * (q & 1), y0 + 8 * (q >> 1), 8, kappa)) m |= 1u << q;
+  return m;
 }
 
 // ---- launchers (each returns cudaError_t of the launch) ------------------
@@ -201,10 +217,12 @@ cudaError_t launch_dense_bwd(const Rec *rec, int64_t M, int B, int d, float l2ta
                              const float *dproj, float *mom, cudaStream_t st);
 
 // gem_ctf.cu
+// Radix sequence of an n-point FFT, 2 bits per stage (0: radix 2,
+// 1: radix 3, 2: radix 4), first stage in the low bits.
 struct FftPlan {
   int n;
   int nst;
-  int radix[16];
+  unsigned code;
 };
 bool fft_plan(int n, FftPlan &p);
 cudaError_t ctf_configure(int d);

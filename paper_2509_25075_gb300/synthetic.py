@@ -47,12 +47,17 @@ class Workload:
     norm_mode: int = 0
     seed: int = 0
 
+    def __post_init__(self):
+        # the library takes apix as float32: hold the float32 value so that
+        # every consumer sees the same number
+        object.__setattr__(self, "apix", float(np.float32(self.apix)))
+
     @property
     def tau(self) -> float:
         """Threshold of Eq. accu: 1e-4 of the largest possible 2D peak
-        (rho_max / (2 pi s_min^2)) of this recipe."""
+        (rho_max / (2 pi s_min^2)) of this recipe, rounded to float32."""
         s_min = self.s_lo * self.apix
-        return 1e-4 * 1.5 / (2.0 * math.pi * s_min * s_min)
+        return float(np.float32(1e-4 * 1.5 / (2.0 * math.pi * s_min * s_min)))
 
     def as_config(self) -> dict:
         c = asdict(self)

@@ -159,8 +159,10 @@ def test_ctf_loss_matches_oracle(d, B, form):
     np.testing.assert_allclose(li.cpu().numpy(), oli, rtol=1e-5)
     p = pred.cpu().numpy()
     assert np.max(np.abs(p - opred)) <= 1e-5 * np.max(np.abs(opred))
+    # dL/dproj feeds sums with heavy cancellation in the gradient, whose
+    # per-entry check needs it to about 1e-6 of its maximum
     g = dproj.cpu().numpy()
-    assert np.max(np.abs(g - og)) <= 1e-5 * np.max(np.abs(og))
+    assert np.max(np.abs(g - og)) <= 2e-6 * np.max(np.abs(og))
 
 
 @pytest.mark.parametrize("norm_mode", [0, 1])
