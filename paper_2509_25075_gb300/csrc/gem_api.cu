@@ -27,7 +27,7 @@ struct gem_ctx {
   // scratch
   GaussPrep *gp = nullptr;
   Rec *rec = nullptr;
-  float *depth = nullptr;
+
   BinScratch bin{};
   float *mom = nullptr;
   float *part = nullptr;
@@ -168,13 +168,13 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
   const size_t BM = (size_t)g.max_B * (size_t)g.max_M;
   const size_t nchD = bin_chunks_depth(g.max_M), nchT = bin_chunks_tiles(g.max_M);
   c->nbg = g.max_B < 16 ? g.max_B : 16;
-  bool ok = alloc(c, &c->gp, g.max_M) && alloc(c, &c->rec, BM) && alloc(c, &c->depth, BM) &&
-            alloc(c, &c->bin.keyA, BM) && alloc(c, &c->bin.keyB, BM) &&
-            alloc(c, &c->bin.valA, BM) && alloc(c, &c->bin.valB, BM) &&
+  bool ok = alloc(c, &c->gp, g.max_M) && alloc(c, &c->rec, BM) && alloc(c, &c->bin.key, BM) &&
+            alloc(c, &c->bin.packed, BM) && alloc(c, &c->bin.perm, BM) &&
             alloc(c, &c->bin.dcnt, (size_t)g.max_B * nchD * 256) &&
             alloc(c, &c->bin.tcnt, (size_t)g.max_B * nchT * c->T) &&
             alloc(c, &c->bin.tile_start, (size_t)g.max_B * c->T + 1) &&
-            alloc(c, &c->bin.list, (size_t)c->cfg.max_pairs) && alloc(c, &c->mom, BM * 6) &&
+            alloc(c, &c->bin.list, (size_t)c->cfg.max_pairs) &&
+            alloc(c, &c->bin.lmask, (size_t)c->cfg.max_pairs) && alloc(c, &c->mom, BM * 6) &&
             alloc(c, &c->part, (size_t)c->nbg * g.max_M * kNpar) &&
             alloc(c, &c->proj, (size_t)g.max_B * d * d) &&
             alloc(c, &c->dproj, (size_t)g.max_B * d * d) &&
@@ -262,8 +262,10 @@ static int prep(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   const gem_config &g = c->cfg;
   if ((e = launch_gauss_prep(params, M, g.norm_mode, c->gp, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "gauss_prep");
-  if ((e = launch_view_prep(c->gp, M, B, R, t, g.apix, g.d, c->l2tau, c->rec, c->depth,
-                            c->stream)) != cudaSuccess)
+  // depth keys span [-d apix, d apix]: the half-diagonal of the box is shorter
+  const float zrange = (float)g.d * g.apix;
+  if ((e = launch_view_prep(c->gp, M, B, R, t, g.apix, g.d, c->l2tau, zrange, c->rec,
+                            c->bin.key, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "view_prep");
   c->params = params;
   c->R = R;
@@ -283,17 +285,15 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   cudaError_t e;
   const gem_config &g = c->cfg;
   const uint32_t *perm = nullptr;
-  // depth keys span [-d apix, d apix]: the half-diagonal of the box is shorter
-  float zrange = (float)g.d * g.apix;
   {
-    StageScope sc(c, GEM_STAGE_BIN, g.zsort ? 11 : 4);
-    if ((e = launch_bin(c->rec, c->depth, M, B, g.d, c->l2tau, zrange, g.zsort, c->bin, &perm,
+    StageScope sc(c, GEM_STAGE_BIN, g.zsort ? 10 : 4);
+    if ((e = launch_bin(c->rec, c->bin.key, M, B, g.d, c->l2tau, g.zsort, c->bin, &perm,
                         c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "bin");
   }
   {
     StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
-    if ((e = launch_raster_fwd(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, M, B, g.d,
+    if ((e = launch_raster_fwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, M, B, g.d,
                                c->l2tau, proj, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "raster_fwd");
   }
@@ -350,7 +350,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     if (dense)
       e = launch_dense_bwd(c->rec, c->M, c->B, g.d, c->l2tau, dproj, c->mom, c->stream);
     else
-      e = launch_raster_bwd(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, c->M, c->B,
+      e = launch_raster_bwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, c->M, c->B,
                             g.d, c->l2tau, dproj, c->mom, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
@@ -422,7 +422,8 @@ int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t li
 int gem_inspect_records(gem_ctx *c, float *out) {
   if (!c || !out) return GEM_EINVAL;
   if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
-  cudaError_t e = launch_inspect_records(c->rec, c->depth, c->M, c->B, out, c->stream);
+  cudaError_t e = launch_inspect_records(c->rec, c->gp, c->M, c->B, c->R, c->t, c->cfg.apix,
+                                         c->cfg.d, out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "inspect records");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "synchronise");
@@ -436,7 +437,7 @@ int gem_pair_stats(gem_ctx *c, int64_t *kept, int64_t *evaluated) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->kept, 0, 2 * sizeof(unsigned long long), c->stream)) !=
           cudaSuccess ||
-      (e = launch_count_kept(c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, c->M, c->B,
+      (e = launch_count_kept(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, c->M, c->B,
                              g.d, c->l2tau, c->kept, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "pair count");

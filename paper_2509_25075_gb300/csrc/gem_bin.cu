@@ -4,52 +4,53 @@
 // Sec. 3.2 (after Eq. accu) sorts the selected Gaussians along z and
 // accumulates from the lowest z to the highest.  Here:
 //   1. per image, a stable sort of the Gaussians by a 16-bit depth key
-//      (two 8-bit counting passes; ties keep index order), giving a rank;
+//      (written by the preprocess; two 8-bit counting passes, ties keep
+//      index order), giving each image's depth order;
 //   2. a stable counting sort of the (Gaussian, tile) incidences by tile,
-//      fed in rank order, so every tile list comes out in depth order.
+//      fed in depth order, so every tile list comes out in depth order.
 // Both are chunked counting sorts: count per chunk, scan per image and bin
 // across chunks, then scatter with a rank inside the chunk that preserves
 // input order.  The result is deterministic: no position depends on thread
-// timing.
+// timing.  Each list entry also gets the mask of the 4x4 pixel blocks of
+// its tile that the Gaussian's region above tau meets.
 #include "gem_internal.cuh"
 
 namespace gem {
 
-constexpr int kChunkD = 1024;  // elements per chunk, depth passes
-constexpr int kChunkT = 256;   // Gaussians per chunk, tile binning
+constexpr int kChunkD = 4096;   // elements per chunk, depth passes
+constexpr int kDThreads = 512;  // 16 warps x 256 elements
+constexpr int kChunkT = 256;    // Gaussians per chunk, tile binning
 
 size_t bin_chunks_depth(int64_t M) { return (size_t)((M + kChunkD - 1) / kChunkD); }
 size_t bin_chunks_tiles(int64_t M) { return (size_t)((M + kChunkT - 1) / kChunkT); }
 
-// ------------------------------------------------------ depth key -------
+// ------------------------------------------------ depth passes ---------
 
-__global__ void __launch_bounds__(256) depth_key_kernel(const float *__restrict__ depth,
-                                                        int64_t n, float inv_range,
-                                                        uint16_t *__restrict__ key) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  // map [-range, range] onto 0..65535; out-of-range depths clamp
-  float z = depth[i] * inv_range;
-  float k = floorf((z + 1.f) * 32768.f);
-  k = fminf(fmaxf(k, 0.f), 65535.f);
-  key[i] = (uint16_t)k;
+// Digit of element i: pass 0 reads the low byte of the 16-bit key; pass 1
+// reads the high byte carried in the top 8 bits of the packed word
+// (high byte << 24 | Gaussian index) that pass 0 wrote.
+template <int kPass>
+__device__ __forceinline__ unsigned digit_of(const uint16_t *__restrict__ key,
+                                             const uint32_t *__restrict__ packed, int64_t i) {
+  if (kPass == 0) return key[i] & 255u;
+  return packed[i] >> 24;
 }
 
-// ------------------------------------------------ counting pass --------
-
-// Histogram of one 8-bit digit per chunk: cnt[b][c][256].
-__global__ void __launch_bounds__(256) digit_count_kernel(const uint16_t *__restrict__ key,
-                                                          int64_t M, int shift, int nch,
-                                                          uint32_t *__restrict__ cnt) {
+// Histogram of the pass's digit per chunk: cnt[b][c][256].
+template <int kPass>
+__global__ void __launch_bounds__(kDThreads) digit_count_kernel(
+    const uint16_t *__restrict__ key, const uint32_t *__restrict__ packed, int64_t M, int nch,
+    uint32_t *__restrict__ cnt) {
   __shared__ uint32_t h[256];
   int c = blockIdx.x, b = blockIdx.y;
-  h[threadIdx.x] = 0;
+  if (threadIdx.x < 256) h[threadIdx.x] = 0;
   __syncthreads();
   int64_t base = (int64_t)b * M + (int64_t)c * kChunkD;
   int64_t lim = min((int64_t)kChunkD, M - (int64_t)c * kChunkD);
-  for (int i = threadIdx.x; i < lim; i += 256) atomicAdd(&h[(key[base + i] >> shift) & 255], 1u);
+  for (int i = threadIdx.x; i < lim; i += kDThreads)
+    atomicAdd(&h[digit_of<kPass>(key, packed, base + i)], 1u);
   __syncthreads();
-  cnt[((int64_t)b * nch + c) * 256 + threadIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < 256) cnt[((int64_t)b * nch + c) * 256 + threadIdx.x] = h[threadIdx.x];
 }
 
 // Turn cnt[b][c][bin] into the output offset (within image b) of the first
@@ -64,7 +65,6 @@ __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *__restrict__ 
     col[(int64_t)c * 256] = run;
     run += v;
   }
-  // exclusive scan of the bin totals across the block
   __shared__ uint32_t tot[256];
   tot[bin] = run;
   __syncthreads();
@@ -78,60 +78,81 @@ __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *__restrict__ 
   for (int c = 0; c < nch; ++c) col[(int64_t)c * 256] += base;
 }
 
-// Stable scatter.  Warp w of the block owns elements [128 w, 128 w + 128) of
+// Lanes of the warp holding the same 9-bit value: one ballot per bit.
+__device__ __forceinline__ unsigned same_value_lanes(int v) {
+  unsigned p = 0xffffffffu;
+#pragma unroll
+  for (int bit = 0; bit < 9; ++bit) {
+    const bool set = (v >> bit) & 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, set);
+    p &= set ? bal : ~bal;
+  }
+  return p;
+}
+
+// Stable scatter.  Warp w of the block owns elements [256 w, 256 w + 256) of
 // the chunk and visits them in order, 32 at a time; lanes holding the same
-// digit are ranked by lane with a match mask.  Per-warp digit counts give
-// each warp's base inside the chunk.
-__global__ void __launch_bounds__(256) digit_scatter_kernel(
-    const uint16_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t M, int shift,
-    int nch, const uint32_t *__restrict__ off, uint16_t *__restrict__ kout,
-    uint32_t *__restrict__ vout) {
-  __shared__ uint32_t wc[8][256];
+// digit are ranked by lane with a peer mask.  Per-warp digit counts give
+// each warp's base inside the chunk.  Pass 0 writes (high byte << 24 | j),
+// pass 1 writes j: the image's depth order.
+template <int kPass>
+__global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
+    const uint16_t *__restrict__ key, const uint32_t *__restrict__ packed, int64_t M, int nch,
+    const uint32_t *__restrict__ off, uint32_t *__restrict__ out) {
+  constexpr int kWarps = kDThreads / 32;
+  constexpr int kPer = kChunkD / kWarps;  // 256
+  __shared__ uint32_t wc[kWarps][256];
   int c = blockIdx.x, b = blockIdx.y;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < 8 * 256; i += 256) (&wc[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kDThreads) (&wc[0][0])[i] = 0;
   __syncthreads();
-  int64_t cbase = (int64_t)c * kChunkD;
-  int64_t ibase = (int64_t)b * M;
+  const int64_t cbase = (int64_t)c * kChunkD + warp * kPer;
+  const int64_t ibase = (int64_t)b * M;
   const unsigned lt = (1u << lane) - 1u;
-  // pass 1: per-warp digit counts
-  for (int r = 0; r < 4; ++r) {
-    int64_t e = cbase + warp * 128 + r * 32 + lane;
-    int dig = e < M ? ((kin[ibase + e] >> shift) & 255) : 256 + lane;  // tail lanes never match
-    unsigned peers = __match_any_sync(0xffffffffu, dig);
-    int leader = __ffs(peers) - 1;
-    if (dig < 256 && lane == leader) wc[warp][dig] += __popc(peers);
+  // per-warp digit counts (tail lanes get digits that never match)
+  for (int r = 0; r < kPer / 32; ++r) {
+    int64_t e = cbase + r * 32 + lane;
+    int dig = e < M ? (int)digit_of<kPass>(key, packed, ibase + e) : 256 + lane;
+    unsigned peers = same_value_lanes(dig);
+    if (dig < 256 && lane == __ffs(peers) - 1) wc[warp][dig] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // exclusive prefix over warps, plus the chunk's global offset
-  {
+  // exclusive prefix over warps, plus the chunk's offset
+  if (threadIdx.x < 256) {
     int bin = threadIdx.x;
     uint32_t run = off[((int64_t)b * nch + c) * 256 + bin];
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < kWarps; ++w) {
       uint32_t v = wc[w][bin];
       wc[w][bin] = run;
       run += v;
     }
   }
   __syncthreads();
-  // pass 2: positions
-  for (int r = 0; r < 4; ++r) {
-    int64_t e = cbase + warp * 128 + r * 32 + lane;
+  for (int r = 0; r < kPer / 32; ++r) {
+    int64_t e = cbase + r * 32 + lane;
     bool act = e < M;
-    uint16_t k = act ? kin[ibase + e] : 0;
-    int dig = act ? ((k >> shift) & 255) : 256 + lane;
-    unsigned peers = __match_any_sync(0xffffffffu, dig);
+    uint32_t word = 0;
+    int dig = 256 + lane;
+    if (act) {
+      if (kPass == 0) {
+        uint16_t k = key[ibase + e];
+        dig = k & 255;
+        word = ((uint32_t)(k >> 8) << 24) | (uint32_t)e;
+      } else {
+        word = packed[ibase + e];
+        dig = (int)(word >> 24);
+        word &= 0xffffffu;
+      }
+    }
+    unsigned peers = same_value_lanes(dig);
     int leader = __ffs(peers) - 1;
     uint32_t pos = 0;
     if (act) pos = wc[warp][dig] + __popc(peers & lt);
     __syncwarp();
     if (act && lane == leader) wc[warp][dig] += __popc(peers);
     __syncwarp();
-    if (act && pos < (uint32_t)M) {
-      kout[ibase + pos] = k;
-      vout[ibase + pos] = vin ? vin[ibase + e] : (uint32_t)e;
-    }
+    if (act && pos < (uint32_t)M) out[ibase + pos] = word;
   }
 }
 
@@ -154,72 +175,159 @@ __device__ __forceinline__ bool rec_tiles(const Rec &r, int d, TileRect &tr) {
   return true;
 }
 
-__global__ void __launch_bounds__(256) tile_count_kernel(const Rec *__restrict__ rec,
-                                                         const uint32_t *__restrict__ perm,
-                                                         int64_t M, int d, float l2tau, int nch,
-                                                         uint32_t *__restrict__ tcnt) {
-  extern __shared__ uint32_t tc[];
-  int c = blockIdx.x, b = blockIdx.y;
-  int nt = d / kTile, T = nt * nt;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) tc[i] = 0;
-  __syncthreads();
-  int64_t r = (int64_t)c * kChunkT + threadIdx.x;
+// Shared staging of one chunk of 256 Gaussians (depth order): each
+// Gaussian's record and candidate tile rectangle, and the exclusive prefix
+// of the candidate counts, so that the chunk's (Gaussian, candidate tile)
+// pairs can be spread evenly over the threads whatever the Gaussians' sizes.
+constexpr int kOwnerCap = 8192;  // candidates per chunk with a byte owner map
+
+struct ChunkStage {
+  Ell ell[kChunkT];
+  uint32_t j[kChunkT];
+  int rect[kChunkT];      // tx0 | ty0 << 8 | width << 16 (0 width: no tile)
+  int off[kChunkT + 1];   // exclusive prefix of candidate counts; off[kChunkT] = total
+  int wsum[kChunkT / 32];
+  unsigned char owner[kOwnerCap];  // owner slot of each candidate (when they fit)
+};
+
+__device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict__ rec,
+                                            const uint32_t *__restrict__ perm, int64_t M,
+                                            int b, int c, int d, float l2tau) {
+  const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
+  const int64_t r = (int64_t)c * kChunkT + i;
+  int ncand = 0, packed = 0;
   if (r < M) {
-    uint32_t j = perm ? perm[(int64_t)b * M + r] : (uint32_t)r;
-    Rec rc = rec[(int64_t)b * M + j];
+    const uint32_t j = perm ? perm[(int64_t)b * M + r] : (uint32_t)r;
+    const Rec rc = rec[(int64_t)b * M + j];
+    S.ell[i] = make_ell(rc, l2tau);
+    S.j[i] = j;
     TileRect tr;
     if (rec_tiles(rc, d, tr)) {
-      float kappa = rc.b.y - l2tau + kMargin;
-      for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
-        for (int tx = tr.tx0; tx <= tr.tx1; ++tx)
-          if (tile_hit(rc, tx * kTile, ty * kTile, kappa)) atomicAdd(&tc[ty * nt + tx], 1u);
+      const int w = tr.tx1 - tr.tx0 + 1;
+      ncand = w * (tr.ty1 - tr.ty0 + 1);
+      packed = tr.tx0 | (tr.ty0 << 8) | (w << 16);
     }
   }
-  __syncthreads();
-  uint32_t *dst = tcnt + ((int64_t)b * nch + c) * T;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) dst[i] = tc[i];
-}
-
-// Per (image, tile): exclusive scan of the chunk counts; the tile total goes
-// to tile_n[b * T + t].
-__global__ void __launch_bounds__(256) tile_scan_cols_kernel(uint32_t *__restrict__ tcnt,
-                                                             int nch, int T,
-                                                             int64_t *__restrict__ tile_n) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
-  if (t >= T) return;
-  uint32_t *col = tcnt + (int64_t)b * nch * T + t;
-  uint32_t run = 0;
-  for (int c = 0; c < nch; ++c) {
-    uint32_t v = col[(int64_t)c * T];
-    col[(int64_t)c * T] = run;
-    run += v;
+  S.rect[i] = packed;
+  int inc = ncand;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
   }
-  tile_n[(int64_t)b * T + t] = run;
+  if (lane == 31) S.wsum[warp] = inc;
+  __syncthreads();
+  int base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kChunkT / 32; ++w) {
+    if (w < warp) base += S.wsum[w];
+    total += S.wsum[w];
+  }
+  const int my = base + inc - ncand;
+  S.off[i] = my;
+  if (i == 0) S.off[kChunkT] = total;
+  if (total <= kOwnerCap)
+    for (int q = 0; q < ncand; ++q) S.owner[my + q] = (unsigned char)i;
+  __syncthreads();
 }
 
-// In-place exclusive scan of n counts (one block), total in x[n].  Flags the
-// capacity bit when the total exceeds cap.
+// Owner (Gaussian slot) of candidate k: from the byte map when the chunk's
+// candidates fit it, else the last slot whose offset is <= k.
+__device__ __forceinline__ int candidate_owner(const ChunkStage &S, int k, int total) {
+  if (total <= kOwnerCap) return S.owner[k];
+  int lo = 0, hi = kChunkT - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.off[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per chunk of 256 Gaussians (depth order) of image b: how many hit each
+// tile.  Written transposed, tcnt[b][t][c], so that each tile's column is
+// contiguous for the scan.
+__global__ void __launch_bounds__(kChunkT) tile_count_kernel(const Rec *__restrict__ rec,
+                                                             const uint32_t *__restrict__ perm,
+                                                             int64_t M, int d, float l2tau,
+                                                             int nch, uint32_t *__restrict__ tcnt) {
+  extern __shared__ uint32_t tc[];
+  __shared__ ChunkStage S;
+  const int c = blockIdx.x, b = blockIdx.y;
+  const int nt = d / kTile, T = nt * nt;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) tc[i] = 0;
+  stage_chunk(S, rec, perm, M, b, c, d, l2tau);
+  const int total = S.off[kChunkT];
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    const int o = candidate_owner(S, k, total);
+    const int q = k - S.off[o], pr = S.rect[o];
+    const int w = (pr >> 16) & 0xffff;
+    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    if (tile_hit(S.ell[o], tx * kTile, ty * kTile)) atomicAdd(&tc[ty * nt + tx], 1u);
+  }
+  __syncthreads();
+  uint32_t *dst = tcnt + (int64_t)b * T * nch + c;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) dst[(int64_t)i * nch] = tc[i];
+}
+
+// One warp per (image, tile): exclusive scan of the chunk counts in place;
+// the tile total goes to tile_n[b * T + t].
+__global__ void __launch_bounds__(256) tile_scan_cols_kernel(uint32_t *__restrict__ tcnt,
+                                                             int nch, int64_t ncols,
+                                                             int64_t *__restrict__ tile_n) {
+  int64_t col = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  uint32_t *p = tcnt + col * nch;
+  uint32_t carry = 0;
+  for (int c0 = 0; c0 < nch; c0 += 32) {
+    int c = c0 + lane;
+    uint32_t v = c < nch ? p[c] : 0;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (c < nch) p[c] = carry + inc - v;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) tile_n[col] = carry;
+}
+
+// In-place exclusive scan of n counts (one block of 1024), total in x[n].
+// Flags the capacity bit when the total exceeds cap.
 __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ x, int64_t n,
                                                           int64_t cap, int *__restrict__ status) {
-  __shared__ int64_t part[1024];
+  __shared__ int64_t wtot[32];
   __shared__ int64_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int64_t base = 0; base < n; base += 1024) {
     int64_t i = base + threadIdx.x;
     int64_t v = i < n ? x[i] : 0;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      int64_t u = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-      __syncthreads();
-      part[threadIdx.x] += u;
-      __syncthreads();
+    int64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
     }
-    if (i < n) x[i] = carry + part[threadIdx.x] - v;
+    if (lane == 31) wtot[warp] = inc;
     __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
+    if (warp == 0) {
+      int64_t w = wtot[lane], wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      wtot[lane] = wi - w;  // exclusive prefix over warps
+    }
+    __syncthreads();
+    if (i < n) x[i] = carry + wtot[warp] + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += wtot[31] + inc;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -228,49 +336,51 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
   }
 }
 
-// Scatter: Gaussian i of the chunk (rank order) sets bit i in the bitmap of
+// Scatter: Gaussian i of the chunk (depth order) sets bit i in the bitmap of
 // every tile it hits; its position in a tile's list is the tile's start,
 // plus the chunk's offset for that tile, plus the number of lower bits set.
-__global__ void __launch_bounds__(256) tile_scatter_kernel(
+// Beside the Gaussian's index the entry stores its 4x4-block mask.  The
+// chunk's (Gaussian, candidate tile) pairs are spread over the threads.
+__global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ perm, int64_t M, int d,
     float l2tau, int nch, const uint32_t *__restrict__ tcnt,
-    const int64_t *__restrict__ tile_start, int64_t cap, uint32_t *__restrict__ list) {
+    const int64_t *__restrict__ tile_start, int64_t cap, uint32_t *__restrict__ list,
+    uint16_t *__restrict__ lmask) {
   extern __shared__ uint32_t bm[];  // [T][8]
-  int c = blockIdx.x, b = blockIdx.y;
-  int nt = d / kTile, T = nt * nt;
+  __shared__ ChunkStage S;
+  const int c = blockIdx.x, b = blockIdx.y;
+  const int nt = d / kTile, T = nt * nt;
   for (int i = threadIdx.x; i < T * 8; i += blockDim.x) bm[i] = 0;
-  __syncthreads();
-  int64_t r = (int64_t)c * kChunkT + threadIdx.x;
-  int word = threadIdx.x >> 5;
-  uint32_t bit = 1u << (threadIdx.x & 31);
-  Rec rc;
-  TileRect tr;
-  uint32_t j = 0;
-  bool have = false;
-  float kappa = 0.f;
-  if (r < M) {
-    j = perm ? perm[(int64_t)b * M + r] : (uint32_t)r;
-    rc = rec[(int64_t)b * M + j];
-    have = rec_tiles(rc, d, tr);
-    kappa = rc.b.y - l2tau + kMargin;
+  stage_chunk(S, rec, perm, M, b, c, d, l2tau);
+  const int total = S.off[kChunkT];
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    const int o = candidate_owner(S, k, total);
+    const int q = k - S.off[o], pr = S.rect[o];
+    const int w = (pr >> 16) & 0xffff;
+    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    if (tile_hit(S.ell[o], tx * kTile, ty * kTile))
+      atomicOr(&bm[(ty * nt + tx) * 8 + (o >> 5)], 1u << (o & 31));
   }
-  if (have)
-    for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
-      for (int tx = tr.tx0; tx <= tr.tx1; ++tx)
-        if (tile_hit(rc, tx * kTile, ty * kTile, kappa)) atomicOr(&bm[(ty * nt + tx) * 8 + word], bit);
   __syncthreads();
-  if (!have) return;
-  const uint32_t *coff = tcnt + ((int64_t)b * nch + c) * T;
-  for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
-    for (int tx = tr.tx0; tx <= tr.tx1; ++tx) {
-      int t = ty * nt + tx;
-      const uint32_t *w = bm + t * 8;
-      if (!(w[word] & bit)) continue;
-      uint32_t rank = __popc(w[word] & (bit - 1u));
-      for (int k = 0; k < word; ++k) rank += __popc(w[k]);
-      int64_t pos = tile_start[(int64_t)b * T + t] + coff[t] + rank;
-      if (pos < cap) list[pos] = j;
+  const uint32_t *coff = tcnt + (int64_t)b * T * nch + c;
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    const int o = candidate_owner(S, k, total);
+    const int q = k - S.off[o], pr = S.rect[o];
+    const int w = (pr >> 16) & 0xffff;
+    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    const int t = ty * nt + tx;
+    const uint32_t *bw = bm + t * 8;
+    const int word = o >> 5;
+    const uint32_t bit = 1u << (o & 31);
+    if (!(bw[word] & bit)) continue;
+    uint32_t rank = __popc(bw[word] & (bit - 1u));
+    for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk]);
+    const int64_t pos = tile_start[(int64_t)b * T + t] + coff[(int64_t)t * nch] + rank;
+    if (pos < cap) {
+      list[pos] = S.j[o];
+      lmask[pos] = (uint16_t)block_mask16(S.ell[o], tx * kTile, ty * kTile);
     }
+  }
 }
 
 static int tile_smem_bytes(int d) {
@@ -288,36 +398,35 @@ cudaError_t bin_configure(int d) {
   return cudaSuccess;
 }
 
-cudaError_t launch_bin(const Rec *rec, const float *depth, int64_t M, int B, int d,
-                       float l2tau, float zrange, int zsort, BinScratch &s,
-                       const uint32_t **perm_out, cudaStream_t st) {
+cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, int d,
+                       float l2tau, int zsort, BinScratch &s, const uint32_t **perm_out,
+                       cudaStream_t st) {
   cudaError_t e;
   const uint32_t *perm = nullptr;
   if (zsort) {
-    int64_t n = M * B;
-    depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(depth, n, 1.f / zrange, s.keyA);
     int nch = (int)bin_chunks_depth(M);
     dim3 g(nch, B);
-    // low byte, then high byte (LSD); the first pass seeds index order
-    digit_count_kernel<<<g, 256, 0, st>>>(s.keyA, M, 0, nch, s.dcnt);
+    // low byte, then high byte (LSD); ties keep index order
+    digit_count_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, s.dcnt);
     digit_scan_kernel<<<B, 256, 0, st>>>(s.dcnt, nch);
-    digit_scatter_kernel<<<g, 256, 0, st>>>(s.keyA, nullptr, M, 0, nch, s.dcnt, s.keyB, s.valA);
-    digit_count_kernel<<<g, 256, 0, st>>>(s.keyB, M, 8, nch, s.dcnt);
+    digit_scatter_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, s.dcnt, s.packed);
+    digit_count_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, s.packed, M, nch, s.dcnt);
     digit_scan_kernel<<<B, 256, 0, st>>>(s.dcnt, nch);
-    digit_scatter_kernel<<<g, 256, 0, st>>>(s.keyB, s.valA, M, 8, nch, s.dcnt, s.keyA, s.valB);
+    digit_scatter_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, s.packed, M, nch, s.dcnt, s.perm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    perm = s.valB;
+    perm = s.perm;
   }
   int nt = d / kTile, T = nt * nt;
   int nch = (int)bin_chunks_tiles(M);
   dim3 g(nch, B);
   int cnt_smem = T * (int)sizeof(uint32_t);
   tile_count_kernel<<<g, 256, cnt_smem, st>>>(rec, perm, M, d, l2tau, nch, s.tcnt);
-  dim3 gs((T + 255) / 256, B);
-  tile_scan_cols_kernel<<<gs, 256, 0, st>>>(s.tcnt, nch, T, s.tile_start);
-  scan_tiles_kernel<<<1, 1024, 0, st>>>(s.tile_start, (int64_t)B * T, s.cap, s.status);
+  int64_t ncols = (int64_t)B * T;
+  tile_scan_cols_kernel<<<(unsigned)((ncols + 7) / 8), 256, 0, st>>>(s.tcnt, nch, ncols,
+                                                                      s.tile_start);
+  scan_tiles_kernel<<<1, 1024, 0, st>>>(s.tile_start, ncols, s.cap, s.status);
   tile_scatter_kernel<<<g, 256, tile_smem_bytes(d), st>>>(rec, perm, M, d, l2tau, nch, s.tcnt,
-                                                         s.tile_start, s.cap, s.list);
+                                                         s.tile_start, s.cap, s.list, s.lmask);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *perm_out = perm;
   return cudaSuccess;

@@ -59,12 +59,18 @@ cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, Gau
   return cudaGetLastError();
 }
 
+// 16-bit depth key: [-range, range] onto 0..65535 (out-of-range depths clamp).
+__device__ __forceinline__ uint16_t depth_key(float z, float inv_range) {
+  float k = floorf((z * inv_range + 1.f) * 32768.f);
+  return (uint16_t)fminf(fmaxf(k, 0.f), 65535.f);
+}
+
 __global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restrict__ gp,
                                                         int64_t M, const float *__restrict__ R,
                                                         const float *__restrict__ t,
                                                         float apix, int d, float l2tau,
-                                                        Rec *__restrict__ rec,
-                                                        float *__restrict__ depth) {
+                                                        float inv_range, Rec *__restrict__ rec,
+                                                        uint16_t *__restrict__ key) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (j >= M) return;
@@ -93,23 +99,30 @@ __global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restr
     r.b = make_float4(0.f, -INFINITY, -1.f, -1.f);
   }
   rec[(int64_t)b * M + j] = r;
-  depth[(int64_t)b * M + j] = v.depth;
+  key[(int64_t)b * M + j] = depth_key(v.depth, inv_range);
 }
 
 cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
-                             const float *t, float apix, int d, float l2tau, Rec *rec,
-                             float *depth, cudaStream_t st) {
+                             const float *t, float apix, int d, float l2tau, float zrange,
+                             Rec *rec, uint16_t *key, cudaStream_t st) {
   dim3 grid((unsigned)((M + 255) / 256), (unsigned)B);
-  view_prep_kernel<<<grid, 256, 0, st>>>(gp, M, R, t, apix, d, l2tau, rec, depth);
+  view_prep_kernel<<<grid, 256, 0, st>>>(gp, M, R, t, apix, d, l2tau, 1.f / zrange, rec, key);
   return cudaGetLastError();
 }
 
 __global__ void inspect_records_kernel(const Rec *__restrict__ rec,
-                                       const float *__restrict__ depth, int64_t n,
-                                       float *__restrict__ out) {
+                                       const GaussPrep *__restrict__ gp, int64_t M, int64_t n,
+                                       const float *__restrict__ R, const float *__restrict__ t,
+                                       float apix, int d, float *__restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Rec r = rec[i];
+  int b = (int)(i / M);
+  float Rl[9], tl[2];
+  for (int k = 0; k < 9; ++k) Rl[k] = R[9 * b + k];
+  tl[0] = t[2 * b];
+  tl[1] = t[2 * b + 1];
+  const float depth = view_project(gp[i % M], Rl, tl, apix, d).depth;
   float *o = out + i * 8;
   bool valid = r.b.y > -INFINITY;
   o[0] = r.a.x;
@@ -118,14 +131,16 @@ __global__ void inspect_records_kernel(const Rec *__restrict__ rec,
   o[3] = r.a.w * (-1.f / kLog2e);
   o[4] = r.b.x * (-2.f / kLog2e);
   o[5] = r.b.y;
-  o[6] = depth[i];
+  o[6] = depth;
   o[7] = valid ? 1.f : 0.f;
 }
 
-cudaError_t launch_inspect_records(const Rec *rec, const float *depth, int64_t M, int B,
-                                   float *out, cudaStream_t st) {
+cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t M, int B,
+                                   const float *R, const float *t, float apix, int d, float *out,
+                                   cudaStream_t st) {
   int64_t n = M * B;
-  inspect_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, depth, n, out);
+  inspect_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, gp, M, n, R, t, apix,
+                                                                      d, out);
   return cudaGetLastError();
 }
 

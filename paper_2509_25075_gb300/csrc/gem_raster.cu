@@ -2,94 +2,145 @@
 // plus the plain dense forms used as the baseline.
 //
 // Both rasterisers run one CTA of 128 threads per (image, 16x16 tile) and
-// stage the tile's list (depth order) in shared memory 128 records at a
-// time.  The thread that stages a record also computes its quadrant mask:
-// bit q is set when the record's region above tau meets the 8x8 quadrant q
-// of the tile (exact ellipse-rectangle test), so work is spent only where a
-// pair can be kept.
+// walk the tile's list, which is in ascending depth and carries, per entry,
+// the mask of the 4x4 pixel blocks the Gaussian's region above tau meets
+// (computed once by the binning).  A Gaussian therefore costs 16 pixel
+// evaluations per block it touches, instead of 256 per tile.
 //
-// a3: Eq. render restricted by Eq. accu.  Warp q owns quadrant q (8 rows x
-//     8 columns, two horizontally adjacent pixels per lane) and walks, in
-//     list order, only the staged records whose bit q is set (a ballot per
-//     32 records).  Each pixel adds its kept terms from the lowest depth to
-//     the highest.
+// a3: Eq. render restricted by Eq. accu.  The 16 blocks are owned by 8
+//     threads each (two horizontally adjacent pixels per thread).  Records
+//     are staged 128 at a time; ballots give every block the list of staged
+//     records that touch it, in list order, and the block's threads walk
+//     that list.  So each pixel adds its kept terms from the lowest depth to
+//     the highest, deterministically (float partials per 128 records, summed
+//     in double).
 // a5: the "efficient gradient" of Sec. 1 (iii) / Sec. 3.2: only pairs kept by
-//     Eq. accu.  One thread per listed Gaussian; the staged batch is sorted
-//     by quadrant mask so that a warp's threads walk the same quadrants.  The
-//     thread accumulates six moments of g * value over its pixels, which a6
-//     turns into parameter gradients; one set of atomics per (tile, Gaussian).
+//     Eq. accu.  One thread per staged record walks the record's blocks and
+//     accumulates six moments of g * value in registers; the staged batch is
+//     first sorted by block count so that a warp's loops have equal length.
+//     a6 turns the moments into parameter gradients.  One set of vector
+//     atomics per (tile, Gaussian) goes to global memory.
 #include "gem_internal.cuh"
 
 namespace gem {
 
-constexpr int kFwdThreads = 128;
-constexpr int kBwdThreads = 128;
+constexpr int kThreads = 128;
+
+// (sum, compensation) + x, Kahan; the compensated value is sum - compensation.
+__device__ __forceinline__ float2 kahan_add(float2 s, float x) {
+  const float y = x - s.y;
+  const float t = s.x + y;
+  return make_float2(t, (t - s.x) - y);
+}
+constexpr int kWin = 128;  // records staged per window
 
 // kCount = true: the same walk, counting kept pairs into kept[0] and
 // evaluated pairs into kept[1] instead of writing the projection
 // (inspection only, never on the timed path).
 template <bool kCount>
-__global__ void __launch_bounds__(kFwdThreads) raster_fwd_kernel(
+__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
-    const int64_t *__restrict__ tile_start, int64_t cap, int64_t M, int d, float l2tau,
-    float *__restrict__ proj, unsigned long long *__restrict__ kept) {
-  __shared__ float4 sa[kFwdThreads], sb[kFwdThreads];
-  __shared__ unsigned smask[kFwdThreads];
+    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    int64_t M, int d, float l2tau, float *__restrict__ proj,
+    unsigned long long *__restrict__ kept) {
+  __shared__ float4 sa[kWin], sb[kWin];
+  __shared__ unsigned char blist[16][kWin];          // per block: staged slots touching it
+  __shared__ unsigned short wcnt[kThreads / 32][16];  // per warp, per block: how many
+  __shared__ float2 pix[kTile * kTile];               // per-pixel compensated sums over windows
+  __shared__ unsigned char sorder[16], slen[16];      // blocks by list length
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned qbit = 1u << warp;
-  // quadrant (warp & 1, warp >> 1); lane -> row lane/4, columns 2 (lane%4) + {0,1}
-  const int px_ = x0 + 8 * (warp & 1) + 2 * (lane & 3);
-  const int py_ = y0 + 8 * (warp >> 1) + (lane >> 2);
-  const float X0 = (float)px_, X1 = X0 + 1.f, Y = (float)py_;
+  // thread group g (8 threads) takes, in each window, the block with the
+  // g-th longest list; within it, pair pp: row pp/2, columns 2 (pp%2) + {0,1}
+  const int grp = threadIdx.x >> 3, pp = threadIdx.x & 7;
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
   s = min(s, e);
   const Rec *rb = rec + (int64_t)b * M;
-  double acc0 = 0.0, acc1 = 0.0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < kTile * kTile; i += kThreads) pix[i] = make_float2(0.f, 0.f);
   unsigned nkept = 0, neval = 0;
-  for (int64_t base = s; base < e; base += kFwdThreads) {
-    const int n = (int)min((int64_t)kFwdThreads, e - base);
-    __syncthreads();
+  for (int64_t base = s; base < e; base += kWin) {
+    const int n = (int)min((int64_t)kWin, e - base);
+    __syncthreads();  // previous window fully consumed
+    unsigned m = 0;
     if (threadIdx.x < n) {
       const Rec r = rb[list[base + threadIdx.x]];
+      m = lmask[base + threadIdx.x];
       sa[threadIdx.x] = r.a;
       sb[threadIdx.x] = r.b;
-      smask[threadIdx.x] = quadrant_mask(r, x0, y0, r.b.y - l2tau + kMargin);
-    } else {
-      smask[threadIdx.x] = 0;
     }
+    unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      unsigned bk = __ballot_sync(0xffffffffu, (m >> k) & 1u);
+      if (lane == k) mybal = bk;
+    }
+    if (lane < 16) wcnt[warp][lane] = (unsigned short)__popc(mybal);
     __syncthreads();
-    float p0 = 0.f, p1 = 0.f;
-    for (int c = 0; c < n; c += 32) {
-      unsigned bal = __ballot_sync(0xffffffffu, smask[c + lane] & qbit);
-      while (bal) {
-        const int k = c + __ffs(bal) - 1;
-        bal &= bal - 1;
-        const float4 A = sa[k];
-        const float4 Bv = sb[k];
-        const float dy = Y - A.y;
-        const float bdy = A.w * dy;
-        const float cdy = fmaf(Bv.x * dy, dy, Bv.y);
-        const float dx0 = X0 - A.x, dx1 = X1 - A.x;
-        const float e0 = fmaf(fmaf(A.z, dx0, bdy), dx0, cdy);
-        const float e1 = fmaf(fmaf(A.z, dx1, bdy), dx1, cdy);
-        if (kCount) {
-          nkept += (e0 > l2tau) + (e1 > l2tau);
-          neval += 2;
-        } else {
-          const float v0 = ex2_approx(e0), v1 = ex2_approx(e1);
-          p0 += e0 > l2tau ? v0 : 0.f;
-          p1 += e1 > l2tau ? v1 : 0.f;
-        }
+    // place my record in the lists of its blocks: after the records of lower
+    // warps and lower lanes touching the same block
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const unsigned bk = __shfl_sync(0xffffffffu, mybal, k);
+      if ((m >> k) & 1u) {
+        int pos = __popc(bk & lt);
+        for (int w = 0; w < warp; ++w) pos += wcnt[w][k];
+        blist[k][pos] = (unsigned char)threadIdx.x;
       }
     }
-    acc0 += (double)p0;
-    acc1 += (double)p1;
+    // warp 0 orders the blocks by list length (longest first, ties by
+    // index): group g takes block sorder[g]
+    if (warp == 0) {
+      int len = 0;
+      if (lane < 16)
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) len += wcnt[w][lane];
+      int rank = 0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int lq = __shfl_sync(0xffffffffu, len, q);
+        rank += (lq > len) || (lq == len && q < lane);
+      }
+      if (lane < 16) {
+        sorder[rank] = (unsigned char)lane;
+        slen[rank] = (unsigned char)len;
+      }
+    }
+    __syncthreads();
+    const int blk = sorder[grp], nb = slen[grp];
+    const int px_ = x0 + 4 * (blk & 3) + 2 * (pp & 1);
+    const int py_ = y0 + 4 * (blk >> 2) + (pp >> 1);
+    const float X0 = (float)px_, X1 = X0 + 1.f, Y = (float)py_;
+    float p0 = 0.f, p1 = 0.f;
+    for (int i = 0; i < nb; ++i) {
+      const int slot = blist[blk][i];
+      const float4 A = sa[slot];
+      const float4 Bv = sb[slot];
+      const float dy = Y - A.y;
+      const float bdy = A.w * dy;
+      const float cdy = fmaf(Bv.x * dy, dy, Bv.y);
+      const float dx0 = X0 - A.x, dx1 = X1 - A.x;
+      const float e0 = fmaf(fmaf(A.z, dx0, bdy), dx0, cdy);
+      const float e1 = fmaf(fmaf(A.z, dx1, bdy), dx1, cdy);
+      if (kCount) {
+        nkept += (e0 > l2tau) + (e1 > l2tau);
+        neval += 2;
+      } else {
+        const float v0 = ex2_approx(e0), v1 = ex2_approx(e1);
+        p0 += e0 > l2tau ? v0 : 0.f;
+        p1 += e1 > l2tau ? v1 : 0.f;
+      }
+    }
+    // the window's sum joins the pixel's running sum (one owner per pixel
+    // per window, windows in list order; Kahan-compensated)
+    const int pl = (py_ - y0) * kTile + (px_ - x0);
+    pix[pl] = kahan_add(pix[pl], p0);
+    pix[pl + 1] = kahan_add(pix[pl + 1], p1);
   }
   if (kCount) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -102,48 +153,52 @@ __global__ void __launch_bounds__(kFwdThreads) raster_fwd_kernel(
     }
     return;
   }
-  float2 out = make_float2((float)acc0, (float)acc1);
-  *reinterpret_cast<float2 *>(proj + ((int64_t)b * d + py_) * d + px_) = out;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTile * kTile / 2; i += kThreads) {
+    const int r = (2 * i) / kTile, c = (2 * i) % kTile;
+    *reinterpret_cast<float2 *>(proj + ((int64_t)b * d + y0 + r) * d + x0 + c) =
+        make_float2(pix[2 * i].x - pix[2 * i].y, pix[2 * i + 1].x - pix[2 * i + 1].y);
+  }
 }
 
-cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
-                              int64_t cap, int64_t M, int B, int d, float l2tau, float *proj,
-                              cudaStream_t st) {
+cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+                              const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
+                              float l2tau, float *proj, cudaStream_t st) {
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
-  raster_fwd_kernel<false><<<grid, kFwdThreads, 0, st>>>(rec, list, tile_start, cap, M, d,
-                                                         l2tau, proj, nullptr);
+  raster_fwd_kernel<false><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                      l2tau, proj, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
-                              int64_t cap, int64_t M, int B, int d, float l2tau,
-                              unsigned long long *kept, cudaStream_t st) {
+cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+                              const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
+                              float l2tau, unsigned long long *kept, cudaStream_t st) {
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
-  raster_fwd_kernel<true><<<grid, kFwdThreads, 0, st>>>(rec, list, tile_start, cap, M, d,
-                                                        l2tau, nullptr, kept);
+  raster_fwd_kernel<true><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                     l2tau, nullptr, kept);
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kBwdThreads) raster_bwd_kernel(
+__global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
-    const int64_t *__restrict__ tile_start, int64_t cap, int64_t M, int d, float l2tau,
-    const float *__restrict__ dproj, float *__restrict__ mom) {
-  __shared__ float4 sg[kTile][kTile / 4];
-  __shared__ float4 sa[kBwdThreads], sb[kBwdThreads];
-  __shared__ uint32_t sj[kBwdThreads];
-  __shared__ unsigned char smask[kBwdThreads];
-  __shared__ int hist[16];
+    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    int64_t M, int d, float l2tau, const float *__restrict__ dproj, float *__restrict__ mom) {
+  __shared__ float4 sg[16][4];  // g by 4x4 block: [block][row] = 4 pixels
+  __shared__ float4 sa[kWin], sb[kWin];
+  __shared__ uint32_t sj[kWin];
+  __shared__ unsigned short smask[kWin];
+  __shared__ int hist[17];
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
-  // g tile: 16 rows x 4 float4
+  // g tile, stored block by block
   if (threadIdx.x < kTile * kTile / 4) {
-    int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-    sg[r][q] = *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 +
-                                                 4 * q);
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // pixel row, 4-column group
+    sg[4 * (r >> 2) + q][r & 3] =
+        *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 + 4 * q);
   }
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
@@ -151,25 +206,27 @@ __global__ void __launch_bounds__(kBwdThreads) raster_bwd_kernel(
   s = min(s, e);
   const Rec *rb = rec + (int64_t)b * M;
   float *mb = mom + (int64_t)b * M * 6;
-  for (int64_t base = s; base < e; base += kBwdThreads) {
-    const int n = (int)min((int64_t)kBwdThreads, e - base);
+  for (int64_t base = s; base < e; base += kWin) {
+    const int n = (int)min((int64_t)kWin, e - base);
+    __syncthreads();  // previous window fully consumed
+    if (threadIdx.x < 17) hist[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x < 16) hist[threadIdx.x] = 0;
-    __syncthreads();
-    // stage: own record and its quadrant mask, then counting sort by mask
+    // stage, then sort the batch by block count (17 buckets)
     Rec r;
     uint32_t j = 0;
     unsigned m = 0;
+    int cnt = 0;
     if (threadIdx.x < n) {
       j = list[base + threadIdx.x];
       r = rb[j];
-      m = quadrant_mask(r, x0, y0, r.b.y - l2tau + kMargin);
-      atomicAdd(&hist[m], 1);
+      m = lmask[base + threadIdx.x];
+      cnt = __popc(m);
+      atomicAdd(&hist[cnt], 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int run = 0;
-      for (int k = 0; k < 16; ++k) {
+      for (int k = 16; k >= 0; --k) {  // most blocks first
         int v = hist[k];
         hist[k] = run;
         run += v;
@@ -177,46 +234,44 @@ __global__ void __launch_bounds__(kBwdThreads) raster_bwd_kernel(
     }
     __syncthreads();
     if (threadIdx.x < n) {
-      int pos = atomicAdd(&hist[m], 1);
+      // sorted by block count: a warp's threads get neighbouring counts, so
+      // their loops have (nearly) the same length
+      const int pos = atomicAdd(&hist[cnt], 1);
       sa[pos] = r.a;
       sb[pos] = r.b;
       sj[pos] = j;
-      smask[pos] = (unsigned char)m;
+      smask[pos] = (unsigned short)m;
     }
     __syncthreads();
     if (threadIdx.x >= n) continue;
+    const unsigned mk = smask[threadIdx.x];
+    if (!mk) continue;
     const float4 A = sa[threadIdx.x];
     const float4 Bv = sb[threadIdx.x];
-    const unsigned mk = smask[threadIdx.x];
-    const float px = A.x, py = A.y, ca = A.z, cb = A.w, cc = Bv.x, l2A = Bv.y;
-    int vlo, vhi;
-    if (mk == 0 || !pixel_range(py, Bv.w, d, vlo, vhi)) continue;
+    const float ca = A.z, cb = A.w, cc = Bv.x, l2A = Bv.y;
     float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      if (!(mk & (1u << q))) continue;
-      const int qx = 8 * (q & 1), qy = 8 * (q >> 1);
-      const int r0_ = max(vlo - y0, qy), r1_ = min(vhi - y0, qy + 7);
-      for (int rr = r0_; rr <= r1_; ++rr) {
-        const float dy = (float)(y0 + rr) - py;
+    for (unsigned mm = mk; mm; mm &= mm - 1) {
+      const int k = __ffs(mm) - 1;
+      const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
+      const float fy = (float)(y0 + 4 * (k >> 2)) - A.y;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const float dy = fy + (float)rr;
         const float bdy = cb * dy;
         const float cdy = fmaf(cc * dy, dy, l2A);
+        const float4 g4 = sg[k][rr];
+        const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
         float a0 = 0.f, a1 = 0.f, a3 = 0.f;
 #pragma unroll
-        for (int hq = 0; hq < 2; ++hq) {
-          const float4 g4 = sg[rr][(qx >> 2) + hq];
-          const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float dx = (float)(x0 + qx + 4 * hq + k) - px;
-            const float ee = fmaf(fmaf(ca, dx, bdy), dx, cdy);
-            const float val = ex2_approx(ee);
-            const float gv = ee > l2tau ? gq[k] * val : 0.f;
-            a0 += gv;
-            const float tt = gv * dx;
-            a1 += tt;
-            a3 = fmaf(tt, dx, a3);
-          }
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const float dx = fx + (float)c4;
+          const float ee = fmaf(fmaf(ca, dx, bdy), dx, cdy);
+          const float val = ex2_approx(ee);
+          const float gv = ee > l2tau ? gq[c4] * val : 0.f;
+          a0 += gv;
+          const float tt = gv * dx;
+          a1 += tt;
+          a3 = fmaf(tt, dx, a3);
         }
         m0 += a0;
         m1 += a1;
@@ -226,23 +281,20 @@ __global__ void __launch_bounds__(kBwdThreads) raster_bwd_kernel(
         m5 = fmaf(dy * dy, a0, m5);
       }
     }
-    float *mm = mb + (int64_t)sj[threadIdx.x] * 6;
-    atomicAdd(mm + 0, m0);
-    atomicAdd(mm + 1, m1);
-    atomicAdd(mm + 2, m2);
-    atomicAdd(mm + 3, m3);
-    atomicAdd(mm + 4, m4);
-    atomicAdd(mm + 5, m5);
+    float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[threadIdx.x] * 6);
+    atomicAdd(mo + 0, make_float2(m0, m1));
+    atomicAdd(mo + 1, make_float2(m2, m3));
+    atomicAdd(mo + 2, make_float2(m4, m5));
   }
 }
 
-cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const int64_t *tile_start,
-                              int64_t cap, int64_t M, int B, int d, float l2tau,
-                              const float *dproj, float *mom, cudaStream_t st) {
+cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+                              const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
+                              float l2tau, const float *dproj, float *mom, cudaStream_t st) {
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
-  raster_bwd_kernel<<<grid, kBwdThreads, 0, st>>>(rec, list, tile_start, cap, M, d, l2tau,
-                                                  dproj, mom);
+  raster_bwd_kernel<<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d, l2tau,
+                                               dproj, mom);
   return cudaGetLastError();
 }
 

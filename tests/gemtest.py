@@ -49,6 +49,17 @@ def borderline_pairs(inp, w, tau, norm_mode=0, rel=1e-5):
     return counts
 
 
+def kept_pairs(inp, w, tau, norm_mode=0, rel=1e-5):
+    """(pairs with FP64 value > tau, pairs within rel * tau of tau) over all
+    images, by brute force one Gaussian at a time (small cases only)."""
+    kept = border = 0
+    for j in range(inp["params"].shape[0]):
+        img = oracle.project(inp["params"][j:j + 1], inp["R"], inp["t"], w.d, w.apix, 0.0, norm_mode)
+        kept += int(np.sum(img > tau))
+        border += int(np.sum(np.abs(img - tau) <= rel * tau))
+    return kept, border
+
+
 def assert_proj_close(got, ref, tau=0.0, border=None, rel=1e-5):
     got = np.asarray(got, dtype=np.float64)
     scale = np.max(np.abs(ref))

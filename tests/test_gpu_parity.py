@@ -100,6 +100,19 @@ def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
 
 
 @pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+def test_kept_pair_count_matches_brute_force(w):
+    """The rasteriser's walk (tile lists + 4x4 block masks) finds every pair
+    whose value exceeds tau: its kept count equals the oracle's brute-force
+    count up to pairs within float32 reach of tau."""
+    inp = gt.inputs(w)
+    ctx, _, _ = _project(w, inp)
+    kept, evaluated = ctx.gem_pair_stats()
+    ref, border = gt.kept_pairs(inp, w, w.tau)
+    assert abs(kept - ref) <= border, (kept, ref, border)
+    assert evaluated >= kept
+
+
+@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
 def test_bins_are_deterministic(w):
     inp = gt.inputs(w)
     ctx, args, proj = _project(w, inp)
@@ -199,11 +212,14 @@ def test_full_step_matches_oracle(w):
     assert loss.item() == pytest.approx(L, rel=1e-5)
     G = oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, og)
     gt.assert_grad_close(grad.cpu().numpy(), G)
-    # the autograd wrapper gives the same gradient
+    # the autograd wrapper gives the same gradient (up to the order in which
+    # float atomics add the per-tile moments: the last bits may differ)
     p = T["params"].clone().requires_grad_(True)
     lt = binding.GemLoss.apply(p, T["R"], T["t"], T["ctf_params"], T["images"], ctx)
     lt.backward()
-    np.testing.assert_allclose(p.grad.cpu().numpy(), grad.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    assert lt.item() == loss.item()
+    gt.assert_grad_close(p.grad.double().cpu().numpy(), grad.double().cpu().numpy(),
+                         norm_tol=1e-6, entry_tol=1e-4)
 
 
 def test_forward_is_deterministic():
