@@ -189,6 +189,31 @@ int gem_inspect_records(gem_ctx *ctx, float *out);
  *             (may be NULL). */
 int gem_pair_stats(gem_ctx *ctx, int64_t *kept, int64_t *evaluated);
 
+/* ---- allocation-free variant ---------------------------------------------- */
+
+/* Step a4 (gem_ctf_loss) for callers that cannot allocate device memory at
+ * the point of the call: code running under a fixed memory budget, behind an
+ * allocator that forbids cudaMalloc after start-up, or where a device
+ * allocation's implicit synchronisation is not allowed.  No context and no
+ * allocation: the scratch (spectrum and loss partials) lives in file-scope
+ * device arrays of fixed size that every GPU loading the library holds until
+ * the process exits.  The paper has no counterpart; this is plumbing.
+ *   d, apix      image side and pixel size, the same rules as gem_config;
+ *   B, proj, ctf, ctf_params, images, pred, dproj, loss_img, loss
+ *                exactly as for gem_ctf_loss (caller-owned device memory);
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream).
+ * Limits: B * d * d <= 1,048,576 and B * (ceil((d/2 + 1) / 8) + 1) <= 65,536;
+ * beyond them the call returns GEM_ECAPACITY and launches nothing.  Other bad
+ * arguments return GEM_EINVAL; CUDA failures GEM_ECUDA.
+ * The first call on each device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the same arrays, which keep the last call's
+ * contents (every call rewrites what it reads); calls that overlap on the
+ * GPU (different streams, no ordering between them) race on them. */
+int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float *proj, const float *ctf,
+                        const float *ctf_params, const float *images, float *pred,
+                        float *dproj, double *loss_img, double *loss, void *cuda_stream);
+
 /* ---- per-stage timing ---------------------------------------------------- */
 
 /* Stages of the hot path, as timed by gem_timing_read. */

@@ -71,6 +71,7 @@ SIGNATURES = {
     "gem_pair_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "gem_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
+    "gem_ctf_loss_static": (ctypes.c_int, [_I32, _F, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
