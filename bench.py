@@ -41,6 +41,26 @@ UNIT = "images/s"
 # both rasterisers.
 EX2_PER_CLK_PER_SM = 32
 
+# DRAM bytes (read + write) per launch of each rasteriser at workload A2,
+# from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
+# valid while the rasteriser sources hash to the value they had then.
+CAPTURED_TRAFFIC = {
+    "source_sha256_16": "69c766320dfcaf27",
+    "workload": "A2",
+    "raster_fwd": 305.205760e6 + 18.138624e6,
+    "raster_bwd": 459.932416e6 + 106.398720e6,
+}
+
+
+def raster_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("gem_raster.cu", "gem_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2509_25075_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -338,8 +358,11 @@ def main():
     mhz = clk.get("sm_mhz") or 1455.0
     peak = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # Gpair/s
     achieved = kept / (per_stage[dom] / 1e3) / 1e9
+    traffic = None
+    if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] and w.name == CAPTURED_TRAFFIC["workload"]:
+        traffic = CAPTURED_TRAFFIC[dom]
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
             "peak_note": f"{sms} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {mhz:.0f} MHz median SM clock "
                          f"under load (one SFU exponential per kept pair)",
             "kept_pairs_per_launch": kept, "evaluated_pairs_per_launch": evaluated,
