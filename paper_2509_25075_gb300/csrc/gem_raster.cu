@@ -15,11 +15,13 @@
 //     the highest, deterministically (float partials per 128 records, summed
 //     in double).
 // a5: the "efficient gradient" of Sec. 1 (iii) / Sec. 3.2: only pairs kept by
-//     Eq. accu.  One thread per staged record walks the record's blocks and
-//     accumulates six moments of g * value in registers; the staged batch is
-//     first sorted by block count so that a warp's loops have equal length.
-//     a6 turns the moments into parameter gradients.  One set of vector
-//     atomics per (tile, Gaussian) goes to global memory.
+//     Eq. accu.  Each warp takes every fourth 64-record window of the list,
+//     sorts it by block count and runs it as two rounds of 32 records with
+//     neighbouring counts, one lane per record: the lane walks the record's
+//     blocks and accumulates six moments of g * value in registers.  No
+//     barrier couples the warps.  a6 turns the moments into parameter
+//     gradients.  One set of vector atomics per (tile, Gaussian) goes to
+//     global memory.
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
   __shared__ float4 sa[kWin], sb[kWin];
   __shared__ unsigned char blist[16][kWin];          // per block: staged slots touching it
   __shared__ unsigned short wcnt[kThreads / 32][16];  // per warp, per block: how many
+  __shared__ unsigned wbal[kThreads / 32][16];        // per warp, per block: which lanes
   __shared__ float2 pix[kTile * kTile];               // per-pixel compensated sums over windows
   __shared__ unsigned char sorder[16], slen[16];      // blocks by list length
   const int nt = d / kTile, T = nt * nt;
@@ -80,18 +83,18 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
       unsigned bk = __ballot_sync(0xffffffffu, (m >> k) & 1u);
       if (lane == k) mybal = bk;
     }
-    if (lane < 16) wcnt[warp][lane] = (unsigned short)__popc(mybal);
+    if (lane < 16) {
+      wcnt[warp][lane] = (unsigned short)__popc(mybal);
+      wbal[warp][lane] = mybal;
+    }
     __syncthreads();
     // place my record in the lists of its blocks: after the records of lower
     // warps and lower lanes touching the same block
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const unsigned bk = __shfl_sync(0xffffffffu, mybal, k);
-      if ((m >> k) & 1u) {
-        int pos = __popc(bk & lt);
-        for (int w = 0; w < warp; ++w) pos += wcnt[w][k];
-        blist[k][pos] = (unsigned char)threadIdx.x;
-      }
+    for (unsigned mm = m; mm; mm &= mm - 1) {
+      const int k = __ffs(mm) - 1;
+      int pos = __popc(wbal[warp][k] & lt);
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][k];
+      blist[k][pos] = (unsigned char)threadIdx.x;
     }
     // warp 0 orders the blocks by list length (longest first, ties by
     // index): group g takes block sorder[g]
@@ -185,106 +188,120 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, const float *__restrict__ dproj, float *__restrict__ mom) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kPer = 2;            // records per lane per window
+  constexpr int kWW = 32 * kPer;     // records per warp window
   __shared__ float4 sg[16][4];  // g by 4x4 block: [block][row] = 4 pixels
-  __shared__ float4 sa[kWin], sb[kWin];
-  __shared__ uint32_t sj[kWin];
-  __shared__ unsigned short smask[kWin];
-  __shared__ int hist[17];
+  __shared__ float4 sa[kWarps][kWW], sb[kWarps][kWW];
+  __shared__ uint32_t sj[kWarps][kWW];
+  __shared__ unsigned short smask[kWarps][kWW];
+  __shared__ int hist[kWarps][17];
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // g tile, stored block by block
   if (threadIdx.x < kTile * kTile / 4) {
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // pixel row, 4-column group
     sg[4 * (r >> 2) + q][r & 3] =
         *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 + 4 * q);
   }
+  __syncthreads();
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
   s = min(s, e);
   const Rec *rb = rec + (int64_t)b * M;
   float *mb = mom + (int64_t)b * M * 6;
-  for (int64_t base = s; base < e; base += kWin) {
-    const int n = (int)min((int64_t)kWin, e - base);
-    __syncthreads();  // previous window fully consumed
-    if (threadIdx.x < 17) hist[threadIdx.x] = 0;
-    __syncthreads();
-    // stage, then sort the batch by block count (17 buckets)
-    Rec r;
-    uint32_t j = 0;
-    unsigned m = 0;
-    int cnt = 0;
-    if (threadIdx.x < n) {
-      j = list[base + threadIdx.x];
-      r = rb[j];
-      m = lmask[base + threadIdx.x];
-      cnt = __popc(m);
-      atomicAdd(&hist[cnt], 1);
+  int *h = hist[warp];
+  // warp w takes windows w, w + 4, ... of 64 records; no barrier couples the
+  // warps after the g tile is in place
+  for (int64_t base = s + kWW * warp; base < e; base += kWW * kWarps) {
+    Rec r[kPer];
+    uint32_t j[kPer];
+    unsigned m[kPer];
+    __syncwarp();  // previous window's reads are done
+    if (lane < 17) h[lane] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int64_t i = base + q * 32 + lane;
+      j[q] = 0;
+      m[q] = 0;
+      if (i < e) {
+        j[q] = list[i];
+        r[q] = rb[j[q]];
+        m[q] = lmask[i];
+      }
+      atomicAdd(&h[__popc(m[q])], 1);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    __syncwarp();
+    // exclusive scan of the count histogram, most blocks first
+    if (lane == 0) {
       int run = 0;
-      for (int k = 16; k >= 0; --k) {  // most blocks first
-        int v = hist[k];
-        hist[k] = run;
-        run += v;
+      for (int v = 16; v >= 0; --v) {
+        const int c = h[v];
+        h[v] = run;
+        run += c;
       }
     }
-    __syncthreads();
-    if (threadIdx.x < n) {
-      // sorted by block count: a warp's threads get neighbouring counts, so
-      // their loops have (nearly) the same length
-      const int pos = atomicAdd(&hist[cnt], 1);
-      sa[pos] = r.a;
-      sb[pos] = r.b;
-      sj[pos] = j;
-      smask[pos] = (unsigned short)m;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int pos = atomicAdd(&h[__popc(m[q])], 1);
+      sa[warp][pos] = r[q].a;
+      sb[warp][pos] = r[q].b;
+      sj[warp][pos] = j[q];
+      smask[warp][pos] = (unsigned short)m[q];
     }
-    __syncthreads();
-    if (threadIdx.x >= n) continue;
-    const unsigned mk = smask[threadIdx.x];
-    if (!mk) continue;
-    const float4 A = sa[threadIdx.x];
-    const float4 Bv = sb[threadIdx.x];
-    const float ca = A.z, cb = A.w, cc = Bv.x, l2A = Bv.y;
-    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
-    for (unsigned mm = mk; mm; mm &= mm - 1) {
-      const int k = __ffs(mm) - 1;
-      const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
-      const float fy = (float)(y0 + 4 * (k >> 2)) - A.y;
+    __syncwarp();
+    // rounds of 32 records with neighbouring block counts
+#pragma unroll 1
+    for (int q = 0; q < kPer; ++q) {
+      const int slot = q * 32 + lane;
+      const unsigned mk = smask[warp][slot];
+      if (!mk) continue;
+      const float4 A = sa[warp][slot];
+      const float4 Bv = sb[warp][slot];
+      const float ca = A.z, cb = A.w, cc = Bv.x, l2A = Bv.y;
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
+      for (unsigned mm = mk; mm; mm &= mm - 1) {
+        const int k = __ffs(mm) - 1;
+        const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
+        const float fy = (float)(y0 + 4 * (k >> 2)) - A.y;
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        const float dy = fy + (float)rr;
-        const float bdy = cb * dy;
-        const float cdy = fmaf(cc * dy, dy, l2A);
-        const float4 g4 = sg[k][rr];
-        const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
-        float a0 = 0.f, a1 = 0.f, a3 = 0.f;
+        for (int rr = 0; rr < 4; ++rr) {
+          const float dy = fy + (float)rr;
+          const float bdy = cb * dy;
+          const float cdy = fmaf(cc * dy, dy, l2A);
+          const float4 g4 = sg[k][rr];
+          const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
+          float a0 = 0.f, a1 = 0.f, a3 = 0.f;
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const float dx = fx + (float)c4;
-          const float ee = fmaf(fmaf(ca, dx, bdy), dx, cdy);
-          const float val = ex2_approx(ee);
-          const float gv = ee > l2tau ? gq[c4] * val : 0.f;
-          a0 += gv;
-          const float tt = gv * dx;
-          a1 += tt;
-          a3 = fmaf(tt, dx, a3);
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const float dx = fx + (float)c4;
+            const float ee = fmaf(fmaf(ca, dx, bdy), dx, cdy);
+            const float val = ex2_approx(ee);
+            const float gv = ee > l2tau ? gq[c4] * val : 0.f;
+            a0 += gv;
+            const float tt = gv * dx;
+            a1 += tt;
+            a3 = fmaf(tt, dx, a3);
+          }
+          m0 += a0;
+          m1 += a1;
+          m2 = fmaf(dy, a0, m2);
+          m3 += a3;
+          m4 = fmaf(dy, a1, m4);
+          m5 = fmaf(dy * dy, a0, m5);
         }
-        m0 += a0;
-        m1 += a1;
-        m2 = fmaf(dy, a0, m2);
-        m3 += a3;
-        m4 = fmaf(dy, a1, m4);
-        m5 = fmaf(dy * dy, a0, m5);
       }
+      float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[warp][slot] * 6);
+      atomicAdd(mo + 0, make_float2(m0, m1));
+      atomicAdd(mo + 1, make_float2(m2, m3));
+      atomicAdd(mo + 2, make_float2(m4, m5));
     }
-    float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[threadIdx.x] * 6);
-    atomicAdd(mo + 0, make_float2(m0, m1));
-    atomicAdd(mo + 1, make_float2(m2, m3));
-    atomicAdd(mo + 2, make_float2(m4, m5));
   }
 }
 
