@@ -45,10 +45,10 @@ EX2_PER_CLK_PER_SM = 32
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "69c766320dfcaf27",
+    "source_sha256_16": "375ddc238aaf4986",
     "workload": "A2",
-    "raster_fwd": 305.205760e6 + 18.138624e6,
-    "raster_bwd": 459.932416e6 + 106.398720e6,
+    "raster_fwd": 295.571456e6 + 18.490624e6,
+    "raster_bwd": 386.912768e6 + 93.806592e6,
 }
 
 
