@@ -69,10 +69,15 @@ typedef struct gem_config {
   int64_t max_pairs; /* capacity of the (image, tile, Gaussian) lists; 0 picks 16*max_B*max_M */
   int32_t zsort;     /* 1: accumulate each pixel from the lowest depth z' to the highest      */
                      /*    (Sec. 3.2); 0: in Gaussian index order.  Changes rounding only.    */
-  int32_t reserved;  /* must be 0                                                             */
+  int32_t no_rotation; /* 1: every Gaussian uses R_j = I and q is ignored (its gradient is 0); */
+                       /*    the "No Rotation" ablation of Sec. 4 (Design Choices, Table 4)  */
+  int32_t isotropic;   /* 1: S_j = s_j I with s_j = the first scale entry; the other two are   */
+                       /*    ignored and get zero gradient ("Isotropic Scaling", same table;   */
+                       /*    the paper sets s_j to the nearest-neighbour distance, which       */
+                       /*    gem_nn_distance computes)                                         */
 } gem_config;
 
-/* Fill *cfg with defaults: tau = 0, norm_mode 0, zsort 1, max_pairs 0. */
+/* Fill *cfg with defaults: tau = 0, norm_mode 0, zsort 1, max_pairs 0, no ablation. */
 int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, int64_t max_M);
 
 /* Create a context.  cuda_stream is a cudaStream_t (NULL: the legacy default
@@ -188,6 +193,27 @@ int gem_inspect_records(gem_ctx *ctx, float *out);
  *   evaluated pairs the tiled forward rasteriser evaluates to find them
  *             (may be NULL). */
 int gem_pair_stats(gem_ctx *ctx, int64_t *kept, int64_t *evaluated);
+
+/* ---- beyond the training step ---------------------------------------------- */
+
+/* k nearest neighbours of the Gaussian centres (Sec. 4, Design Choices of
+ * 3DGS for cryo-EM: the isotropic-scaling ablation takes s_j = the distance
+ * of Gaussian j to its nearest neighbour; also a scale initialisation).
+ *   params  device [M][11] (only the centre p, Angstrom, is read), M <= max_M;
+ *   k       1..16;
+ *   dist    device float [M][k]: the k smallest Euclidean distances from
+ *           p_j to the other centres, ascending (INFINITY where fewer than
+ *           k others exist, or where p_j is not finite);
+ *   idx     device int32 [M][k] or NULL: the neighbours' indices, -1 with
+ *           INFINITY.  Among equal distances the smaller index comes first.
+ * Exact (every centre that can be among the k nearest is examined); the
+ * squared distances are float32 sums of squared float32 differences,
+ * rounded in this order.  Centres that are not finite are never neighbours.
+ * Asynchronous on the context's stream; uses the context's grid scratch (it
+ * does not disturb the state kept for gem_backward).  Errors: GEM_EINVAL
+ * (M or k out of range, NULL pointers), GEM_ECUDA. */
+int gem_nn_distance(gem_ctx *ctx, const float *params, int64_t M, int32_t k, float *dist,
+                    int32_t *idx);
 
 /* ---- allocation-free variant ---------------------------------------------- */
 

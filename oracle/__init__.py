@@ -83,27 +83,57 @@ def num_threads() -> int:
     return int(_load().gem_oracle_num_threads())
 
 
-def preprocess(params, R, t, norm_mode: int = 0) -> np.ndarray:
+def constrained(params, no_rotation: bool = False, isotropic: bool = False) -> np.ndarray:
+    """Parameters under the shape constraints of the ablation study (Sec. 4,
+    Design Choices of 3DGS for cryo-EM): "No Rotation" fixes R_j = I, i.e. the
+    quaternion becomes (1, 0, 0, 0); "Isotropic Scaling" enforces
+    S_j = s_j I, with s_j the first scale entry copied to all three."""
+    th = _f64(params).copy()
+    if no_rotation:
+        th[:, 6:10] = (1.0, 0.0, 0.0, 0.0)
+    if isotropic:
+        th[:, 4] = th[:, 3]
+        th[:, 5] = th[:, 3]
+    return th
+
+
+def fold_grad(g_eff, no_rotation: bool = False, isotropic: bool = False) -> np.ndarray:
+    """Chain rule through constrained(): the gradient with respect to the
+    constrained parameters, mapped back to the 11 free ones.  A fixed
+    quaternion has zero gradient; the shared scale collects the three."""
+    g = _f64(g_eff).copy()
+    if no_rotation:
+        g[:, 6:10] = 0.0
+    if isotropic:
+        g[:, 3] = g[:, 3] + g[:, 4] + g[:, 5]
+        g[:, 4] = 0.0
+        g[:, 5] = 0.0
+    return g
+
+
+def preprocess(params, R, t, norm_mode: int = 0, no_rotation=False, isotropic=False) -> np.ndarray:
     """Per (view, Gaussian): [mean x, mean y, cov xx, cov xy, cov yy, amp, depth, valid]."""
-    params, R, t = _f64(params), _f64(R), _f64(t)
+    params, R, t = constrained(params, no_rotation, isotropic), _f64(R), _f64(t)
     M, B = params.shape[0], R.shape[0]
     out = np.zeros((B, M, 8))
     _load().gem_oracle_preprocess(norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(out))
     return out
 
 
-def project(params, R, t, d: int, apix: float, tau: float, norm_mode: int = 0) -> np.ndarray:
+def project(params, R, t, d: int, apix: float, tau: float, norm_mode: int = 0,
+            no_rotation=False, isotropic=False) -> np.ndarray:
     """Eq. render with Eq. accu: [B][d][d] projections."""
-    params, R, t = _f64(params), _f64(R), _f64(t)
+    params, R, t = constrained(params, no_rotation, isotropic), _f64(R), _f64(t)
     M, B = params.shape[0], R.shape[0]
     img = np.zeros((B, d, d))
     _load().gem_oracle_project(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(img))
     return img
 
 
-def project_pixels(params, R, t, d, apix, tau, pix, norm_mode: int = 0) -> np.ndarray:
+def project_pixels(params, R, t, d, apix, tau, pix, norm_mode: int = 0, no_rotation=False,
+                   isotropic=False) -> np.ndarray:
     """Projection at selected flat pixel indices pix = (b*d + v)*d + u."""
-    params, R, t = _f64(params), _f64(R), _f64(t)
+    params, R, t = constrained(params, no_rotation, isotropic), _f64(R), _f64(t)
     pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
     out = np.zeros(pix.shape[0])
     _load().gem_oracle_project_pixels(d, apix, tau, norm_mode, params.shape[0], _ptr(params), R.shape[0],
@@ -163,8 +193,12 @@ def loss(hfull, proj, images):
     return float(L), pred, li, g
 
 
-def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None) -> np.ndarray:
+def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None, no_rotation=False,
+         isotropic=False) -> np.ndarray:
     """dL/dtheta [nsel][11] given g = dL/dproj [B][d][d]."""
+    if no_rotation or isotropic:
+        ge = grad(constrained(params, no_rotation, isotropic), R, t, d, apix, tau, g, norm_mode, sel)
+        return fold_grad(ge, no_rotation, isotropic)
     params, R, t, g = _f64(params), _f64(R), _f64(t), _f64(g)
     M, B = params.shape[0], R.shape[0]
     if sel is None:
@@ -178,7 +212,43 @@ def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None) -> np.ndar
     return out
 
 
-def forward_loss(params, R, t, hfull, images, d, apix, tau, norm_mode: int = 0) -> float:
+def forward_loss(params, R, t, hfull, images, d, apix, tau, norm_mode: int = 0, no_rotation=False,
+                 isotropic=False) -> float:
     """L(theta) through the whole path; used for central differences."""
-    proj = project(params, R, t, d, apix, tau, norm_mode)
+    proj = project(params, R, t, d, apix, tau, norm_mode, no_rotation, isotropic)
     return loss(hfull, proj, images)[0]
+
+
+def nn_distance(pos, k: int):
+    """k nearest neighbours of each centre, by brute force.
+
+    pos: [M][3] centres (float32 values; Sec. 4, Design Choices: the
+    isotropic scale is the distance to the nearest neighbour).  The distance
+    decisions are taken in float32, in the precision the GPU kernel uses:
+    d^2 = ((dx^2 + dy^2) + dz^2), every operation rounded to float32; the k
+    smallest (d^2, index) pairs in lexicographic order; distance =
+    sqrt(d^2) rounded to float32.  Non-finite centres are never neighbours;
+    missing neighbours are (inf, -1).  Returns (dist [M][k] float32,
+    idx [M][k] int64).
+    """
+    p = np.ascontiguousarray(np.asarray(pos, dtype=np.float32))
+    M = p.shape[0]
+    fin = np.all(np.isfinite(p), axis=1)
+    dist = np.full((M, k), np.inf, dtype=np.float32)
+    idx = np.full((M, k), -1, dtype=np.int64)
+    cols = np.arange(M)
+    for i0 in range(0, M, 256):
+        rows = np.arange(i0, min(M, i0 + 256))
+        dd = [p[rows, a][:, None] - p[None, :, a] for a in range(3)]  # float32, rounded
+        d2 = (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2]
+        d2[:, ~fin] = np.inf
+        d2[rows - i0, rows] = np.inf  # not its own neighbour
+        for r, i in enumerate(rows):
+            if not fin[i]:
+                continue
+            order = np.lexsort((cols, d2[r]))[:k]
+            ok = np.isfinite(d2[r][order])
+            n = int(ok.sum())
+            dist[i, :n] = np.sqrt(d2[r][order[:n]])
+            idx[i, :n] = order[:n]
+    return dist, idx

@@ -44,7 +44,8 @@ class gem_config(ctypes.Structure):
         ("max_M", ctypes.c_int64),
         ("max_pairs", ctypes.c_int64),
         ("zsort", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("no_rotation", ctypes.c_int32),
+        ("isotropic", ctypes.c_int32),
     ]
 
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     "gem_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "gem_ctf_loss_static": (ctypes.c_int, [_I32, _F, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gem_nn_distance": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
@@ -126,7 +128,8 @@ class Context:
     """Owns one gem_ctx.  Methods mirror the C calls of the same name."""
 
     def __init__(self, d: int, apix: float, max_B: int, max_M: int, tau: float = 0.0,
-                 norm_mode: int = 0, zsort: int = 1, max_pairs: int = 0, stream=None):
+                 norm_mode: int = 0, zsort: int = 1, max_pairs: int = 0, no_rotation: int = 0,
+                 isotropic: int = 0, stream=None):
         self.lib = load()
         cfg = gem_config()
         self.lib.gem_config_default(ctypes.byref(cfg), d, apix, max_B, max_M)
@@ -134,6 +137,8 @@ class Context:
         cfg.norm_mode = norm_mode
         cfg.zsort = zsort
         cfg.max_pairs = max_pairs
+        cfg.no_rotation = no_rotation
+        cfg.isotropic = isotropic
         self.cfg = cfg
         self.d, self.apix, self.max_B, self.max_M = d, apix, max_B, max_M
         self.device = torch.cuda.current_device()
@@ -251,6 +256,19 @@ class Context:
         k, e = ctypes.c_int64(), ctypes.c_int64()
         self._rc(self.lib.gem_pair_stats(self.h, ctypes.byref(k), ctypes.byref(e)))
         return int(k.value), int(e.value)
+
+    def gem_nn_distance(self, params, k: int, dist=None, idx=None):
+        """-> (dist [M][k] float32, idx [M][k] int32) of the centres' k nearest neighbours."""
+        M = params.shape[0]
+        _check(params, "params", (M, NPAR))
+        if dist is None:
+            dist = torch.empty(M, k, dtype=torch.float32, device=params.device)
+        if idx is None:
+            idx = torch.empty(M, k, dtype=torch.int32, device=params.device)
+        _check(dist, "dist", (M, k))
+        _check(idx, "idx", (M, k), torch.int32)
+        self._rc(self.lib.gem_nn_distance(self.h, _ptr(params), M, k, _ptr(dist), _ptr(idx)))
+        return dist, idx
 
     def gem_timing(self, enable: bool):
         self._rc(self.lib.gem_timing(self.h, 1 if enable else 0))

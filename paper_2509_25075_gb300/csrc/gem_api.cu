@@ -39,6 +39,7 @@ struct gem_ctx {
   double *lossp = nullptr;
   int *status = nullptr;
   unsigned long long *kept = nullptr;
+  KnnScratch knn{};
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -70,6 +71,10 @@ static int cuda_fail(gem_ctx *c, cudaError_t e, const char *what) {
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int shape_flags(const gem_config &g) {
+  return (g.no_rotation ? kNoRotation : 0) | (g.isotropic ? kIsotropic : 0);
+}
 
 // Brackets one stage with events when timing is on and counts its kernels.
 struct StageScope {
@@ -125,6 +130,8 @@ int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, in
   cfg->max_M = max_M;
   cfg->max_pairs = 0;
   cfg->zsort = 1;
+  cfg->no_rotation = 0;
+  cfg->isotropic = 0;
   return GEM_OK;
 }
 
@@ -153,8 +160,10 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
     code = fail(c, GEM_EINVAL, "max_pairs must be >= 0");
   else if (g.zsort != 0 && g.zsort != 1)
     code = fail(c, GEM_EINVAL, "zsort must be 0 or 1");
-  else if (g.reserved != 0)
-    code = fail(c, GEM_EINVAL, "reserved must be 0");
+  else if (g.no_rotation != 0 && g.no_rotation != 1)
+    code = fail(c, GEM_EINVAL, "no_rotation must be 0 or 1");
+  else if (g.isotropic != 0 && g.isotropic != 1)
+    code = fail(c, GEM_EINVAL, "isotropic must be 0 or 1");
   if (code != GEM_OK) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", c->err);
     delete c;
@@ -181,6 +190,13 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->Z, (size_t)g.max_B * d * d) && alloc(c, &c->tw, (size_t)d) &&
             alloc(c, &c->lossp, (size_t)g.max_B * (ctf_partials(d) + 1)) && alloc(c, &c->status, 1) &&
             alloc(c, &c->kept, 2);
+  // nearest-neighbour grid: at most 2 max_M + 64 cells
+  c->knn.cap = 2 * g.max_M + 64;
+  ok = ok && alloc(c, &c->knn.part, 608 * 6) && alloc(c, &c->knn.grid, 1) &&
+       alloc(c, &c->knn.cell, g.max_M) && alloc(c, &c->knn.cnt, c->knn.cap) &&
+       alloc(c, &c->knn.start, c->knn.cap + 1) && alloc(c, &c->knn.fill, c->knn.cap) &&
+       alloc(c, &c->knn.order, g.max_M) &&
+       alloc(c, &c->knn.bsum, (size_t)knn_scan_blocks(c->knn.cap) + 1);
   if (!ok) {
     snprintf(g_create_err, sizeof(g_create_err), "device allocation failed");
     gem_destroy(c);
@@ -260,7 +276,7 @@ static int prep(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   StageScope sc(c, GEM_STAGE_PREP, 2);
   cudaError_t e;
   const gem_config &g = c->cfg;
-  if ((e = launch_gauss_prep(params, M, g.norm_mode, c->gp, c->stream)) != cudaSuccess)
+  if ((e = launch_gauss_prep(params, M, g.norm_mode, shape_flags(g), c->gp, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "gauss_prep");
   // depth keys span [-d apix, d apix]: the half-diagonal of the box is shorter
   const float zrange = (float)g.d * g.apix;
@@ -355,7 +371,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
   StageScope sc(c, GEM_STAGE_PREP_BWD, 2);
-  if ((e = launch_prep_bwd(c->params, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode,
+  if ((e = launch_prep_bwd(c->params, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode, shape_flags(g),
                            c->mom, c->part, c->nbg, grad, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "prep_bwd");
   return GEM_OK;
@@ -479,6 +495,19 @@ int gem_timing_read(gem_ctx *c, float *ms, int64_t *launches) {
     c->recorded[i] = false;
     c->launches[i] = 0;
   }
+  return GEM_OK;
+}
+
+int gem_nn_distance(gem_ctx *c, const float *params, int64_t M, int32_t k, float *dist,
+                    int32_t *idx) {
+  if (!c) return GEM_EINVAL;
+  if (!params || !dist) return fail(c, GEM_EINVAL, "null params or dist");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  if (k < 1 || k > 16) return fail(c, GEM_EINVAL, "k=%d outside 1..16", k);
+  cudaError_t e = launch_knn(params, M, k, c->knn, dist, idx, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "nearest neighbours");
   return GEM_OK;
 }
 

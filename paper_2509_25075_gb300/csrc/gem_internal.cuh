@@ -232,18 +232,45 @@ __device__ __forceinline__ unsigned block_mask16(const Ell &E, int x0, int y0) {
 // ---- launchers (each returns cudaError_t of the launch) ------------------
 
 // gem_prep.cu
-cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, GaussPrep *gp,
-                              cudaStream_t st);
+// Shape constraints of the ablation study (Sec. 4, Design Choices): R_j = I,
+// and S_j = s_j I with s_j the first scale entry.
+constexpr int kNoRotation = 1;
+constexpr int kIsotropic = 2;
+
+cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, int shape,
+                              GaussPrep *gp, cudaStream_t st);
 cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
                              const float *t, float apix, int d, float l2tau, float zrange,
                              Rec *rec, uint16_t *key, cudaStream_t st);
 cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
                             const float *R, const float *t, float apix, int d, int norm_mode,
-                            const float *mom, float *part, int nbg, float *grad,
+                            int shape, const float *mom, float *part, int nbg, float *grad,
                             cudaStream_t st);
 cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t M, int B,
                                    const float *R, const float *t, float apix, int d, float *out,
                                    cudaStream_t st);
+
+// gem_knn.cu
+struct KnnGrid {
+  float lo[3];  // corner of the centres' bounding box
+  float h, ih;  // cell side and its inverse
+  int n[3];     // cells per axis
+  int ncell;
+};
+struct KnnScratch {
+  float *part;     // [nbb][6] partial boxes (nbb <= 608)
+  KnnGrid *grid;
+  int *cell;       // [M] cell of each centre
+  int *cnt;        // [cap] members per cell
+  int *start;      // [cap + 1] first member of each cell in order[]
+  int *fill;       // [cap] scatter cursors
+  int *order;      // [M] centres grouped by cell
+  int *bsum;       // [knn_scan_blocks(cap) + 1]
+  int64_t cap;     // most cells the grid may use
+};
+int knn_scan_blocks(int64_t cap);
+cudaError_t launch_knn(const float *params, int64_t M, int k, const KnnScratch &s, float *dist,
+                       int32_t *idx, cudaStream_t st);
 
 // gem_bin.cu
 struct BinScratch {

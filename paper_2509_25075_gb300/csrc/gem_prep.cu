@@ -11,15 +11,35 @@ namespace gem {
 
 // ---------------------------------------------------------------- a1 -----
 
+// The parameters a Gaussian actually uses: with kNoRotation the quaternion is
+// (1, 0, 0, 0); with kIsotropic all three scales equal the first.
+struct Shape {
+  float s0, s1, s2, qw, qx, qy, qz;
+};
+
+__device__ __forceinline__ Shape effective_shape(const float *th, int shape) {
+  Shape e;
+  e.s0 = th[3];
+  e.s1 = (shape & kIsotropic) ? th[3] : th[4];
+  e.s2 = (shape & kIsotropic) ? th[3] : th[5];
+  const bool fixed = (shape & kNoRotation) != 0;
+  e.qw = fixed ? 1.f : th[6];
+  e.qx = fixed ? 0.f : th[7];
+  e.qy = fixed ? 0.f : th[8];
+  e.qz = fixed ? 0.f : th[9];
+  return e;
+}
+
 __global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict__ params,
-                                                         int64_t M, int norm_mode,
+                                                         int64_t M, int norm_mode, int shape,
                                                          GaussPrep *__restrict__ gp) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   const float *th = params + j * kNpar;
   float p0 = th[0], p1 = th[1], p2 = th[2];
-  float s0 = th[3], s1 = th[4], s2 = th[5];
-  float qw = th[6], qx = th[7], qy = th[8], qz = th[9];
+  const Shape e = effective_shape(th, shape);
+  float s0 = e.s0, s1 = e.s1, s2 = e.s2;
+  float qw = e.qw, qx = e.qx, qy = e.qy, qz = e.qz;
   float rho = th[10];
   float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   bool ok = qn > 0.f && isfinite(qn) && rho > 0.f && isfinite(rho) && isfinite(s0) &&
@@ -52,10 +72,10 @@ __global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict
   gp[j] = g;
 }
 
-cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, GaussPrep *gp,
-                              cudaStream_t st) {
+cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, int shape,
+                              GaussPrep *gp, cudaStream_t st) {
   int blocks = (int)((M + 255) / 256);
-  gauss_prep_kernel<<<blocks, 256, 0, st>>>(params, M, norm_mode, gp);
+  gauss_prep_kernel<<<blocks, 256, 0, st>>>(params, M, norm_mode, shape, gp);
   return cudaGetLastError();
 }
 
@@ -173,7 +193,7 @@ struct Kahan {
 // the summed dL/dSigma.
 __global__ void __launch_bounds__(128) prep_bwd_kernel(
     const float *__restrict__ params, const GaussPrep *__restrict__ gp, int64_t M, int B,
-    const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode,
+    const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode, int shape,
     const float *__restrict__ mom, int per_group, float *__restrict__ part) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int bg = blockIdx.y;
@@ -231,8 +251,9 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   }
   // view-independent part: Sigma = Rq D Rq^T, D = diag(s^2)
   const float *th = params + j * kNpar;
-  float s[3] = {th[3], th[4], th[5]};
-  float qw = th[6], qx = th[7], qy = th[8], qz = th[9], rho = th[10];
+  const Shape e = effective_shape(th, shape);
+  float s[3] = {e.s0, e.s1, e.s2};
+  float qw = e.qw, qx = e.qx, qy = e.qy, qz = e.qz, rho = th[10];
   float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
   float iq = 1.f / qn;
   float w = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
@@ -279,13 +300,16 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   out[0] = DP[0].s;
   out[1] = DP[1].s;
   out[2] = DP[2].s;
-  out[3] = ds[0];
-  out[4] = ds[1];
-  out[5] = ds[2];
-  out[6] = (dw - w * dot) * iq;
-  out[7] = (dx - x * dot) * iq;
-  out[8] = (dy - y * dot) * iq;
-  out[9] = (dz - z * dot) * iq;
+  // a shared isotropic scale collects the three entries' gradients; a fixed
+  // rotation has none
+  const bool iso = (shape & kIsotropic) != 0, fixed = (shape & kNoRotation) != 0;
+  out[3] = iso ? ds[0] + ds[1] + ds[2] : ds[0];
+  out[4] = iso ? 0.f : ds[1];
+  out[5] = iso ? 0.f : ds[2];
+  out[6] = fixed ? 0.f : (dw - w * dot) * iq;
+  out[7] = fixed ? 0.f : (dx - x * dot) * iq;
+  out[8] = fixed ? 0.f : (dy - y * dot) * iq;
+  out[9] = fixed ? 0.f : (dz - z * dot) * iq;
   out[10] = M0.s / rho;
 }
 
@@ -301,13 +325,13 @@ __global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__
 
 cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
                             const float *R, const float *t, float apix, int d, int norm_mode,
-                            const float *mom, float *part, int nbg, float *grad,
+                            int shape, const float *mom, float *part, int nbg, float *grad,
                             cudaStream_t st) {
   int per = (B + nbg - 1) / nbg;
   int groups = (B + per - 1) / per;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)groups);
-  prep_bwd_kernel<<<grid, 128, 0, st>>>(params, gp, M, B, R, t, apix, d, norm_mode, mom, per,
-                                        part);
+  prep_bwd_kernel<<<grid, 128, 0, st>>>(params, gp, M, B, R, t, apix, d, norm_mode, shape, mom,
+                                        per, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t n = M * kNpar;

@@ -55,7 +55,8 @@ def _create(**over):
     ("max_M", 0, "max_M"),
     ("max_pairs", -5, "max_pairs"),
     ("zsort", 3, "zsort"),
-    ("reserved", 1, "reserved"),
+    ("no_rotation", 2, "no_rotation"),
+    ("isotropic", -1, "isotropic"),
 ])
 def test_bad_config_is_rejected_before_device_work(field, value, msg):
     rc, err, h = _create(**{field: value})
