@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--impl", choices=["gem", "reference"], default="gem")
     ap.add_argument("--workload", default="A2")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain dense form")
+    ap.add_argument("--no-query", action="store_true", help="skip timing the density query")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return ap.parse_args()
 
@@ -398,6 +399,36 @@ def main():
         plain = {"value": pv, "unit": UNIT, "speedup_of_tiled": value / ws / pv,
                  "form": "one thread per pixel over all M Gaussians; one thread per (image, Gaussian) over all pixels"}
 
+    # ---- density query on the d^3 grid (Eq. query) -----------------------------
+    query = None
+    if not args.no_query:
+        vol = torch.empty(w.d, w.d, w.d, device=dev)
+        tq = w.tau_query
+        for _ in range(3):
+            ctx.gem_query(D["params"], tq, vol)
+        torch.cuda.synchronize()
+        nq = 10
+        qe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nq)]
+        for i in range(nq):
+            flush.zero_()
+            qe[i][0].record(stream)
+            ctx.gem_query(D["params"], tq, vol)
+            qe[i][1].record(stream)
+        torch.cuda.synchronize()
+        if ctx.gem_status() != 0:
+            raise RuntimeError("device status after the query: " + ctx.lib.gem_last_error(ctx.h).decode())
+        q_ms = sum(a.elapsed_time(b) for a, b in qe) / nq
+        nbatch = -(-w.d // w.B)
+        query = {"ms": q_ms, "voxels_per_s": w.d ** 3 / (q_ms / 1e3), "grid": w.d, "M": w.M, "tau": tq,
+                 "slice_batches": nbatch, "gpu_launches_per_call": 1 + 6 * nbatch,
+                 "l2": "flushed before each call (256 MB write)"}
+        if nbatch == 1:
+            qk, qv = ctx.gem_pair_stats()
+            qa = qk / (q_ms / 1e3) / 1e9
+            query.update({"kept_pairs": qk, "evaluated_pairs": qv,
+                          "roofline": {"bound": "alu", "kernel": "whole query", "achieved": qa, "peak": peak,
+                                       "unit": "Gpair/s", "frac": qa / peak}})
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w)
@@ -409,7 +440,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w), "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "plain": plain,
-            "stages_ms": per_stage, "loss": float(loss.item()),
+            "stages_ms": per_stage, "loss": float(loss.item()), "query": query,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -160,7 +160,8 @@ int gem_backward(gem_ctx *ctx, float *grad);
 /* ---- plain dense forms (no tiles, no binning, no ordering) -------------- */
 
 /* Same result as gem_project, computed by one thread per pixel over all M
- * Gaussians.  Keeps the same state for gem_project_backward_dense. */
+ * Gaussians.  Keeps the same state for gem_project_backward_dense (no tile
+ * lists: gem_project_backward after it returns GEM_ESTATE). */
 int gem_project_dense(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
                       const float *t, float *proj);
 
@@ -170,7 +171,10 @@ int gem_project_backward_dense(gem_ctx *ctx, const float *dproj, float *grad);
 
 /* ---- inspection (synchronise the stream) ------------------------------- */
 
-/* Number of (image, tile, Gaussian) entries the last gem_project listed. */
+/* Number of (image, tile, Gaussian) entries the last binning listed: that of
+ * the last gem_project, or of the last slice batch of gem_query.  The
+ * inspection and pair-statistics calls below read the same lists.
+ * GEM_ESTATE when there are none. */
 int gem_pair_count(gem_ctx *ctx, int64_t *n_pairs);
 
 /* Copy the bins of the last gem_project into caller device memory:
@@ -187,14 +191,35 @@ int gem_inspect_bins(gem_ctx *ctx, int64_t *tile_start, uint32_t *list, int64_t 
  * log2 of the 2D amplitude, depth z' (Angstrom), valid flag (1 or 0). */
 int gem_inspect_records(gem_ctx *ctx, float *out);
 
-/* Pair statistics of the last gem_project, counted by a separate pass over
- * the bins (not part of the hot path; synchronises the stream):
+/* Pair statistics of the last binning (see gem_pair_count), counted by a
+ * separate pass over the bins (not part of the hot path; synchronises the
+ * stream):
  *   kept      (pixel, Gaussian) pairs with value > tau (Eq. accu),
  *   evaluated pairs the tiled forward rasteriser evaluates to find them
  *             (may be NULL). */
 int gem_pair_stats(gem_ctx *ctx, int64_t *kept, int64_t *evaluated);
 
 /* ---- beyond the training step ---------------------------------------------- */
+
+/* Density query (Eq. query, Fig. query): the density of the Gaussians on the
+ * context's d x d x d voxel grid,
+ *   V(x) = sum_j [G_j(x) > tau] G_j(x),
+ *   G_j(x) = A_j exp(-1/2 (x - p_j)^T Sigma_j^-1 (x - p_j))   (Eq. G),
+ * with A_j = rho_j in norm_mode 1 (rho a peak density, Eq. G as printed) and
+ * A_j = rho_j / ((2 pi)^3/2 |Sigma_j|^1/2) in norm_mode 0 (rho a mass: the
+ * density whose line integral is Eq. render).  The ablation flags apply.
+ *   params  device [M][11], M <= max_M (caller-owned);
+ *   tau     threshold on the 3D value (>= 0; 0 keeps every pair);
+ *   vol     device float [d][d][d], written in full: vol[z][y][x] is the
+ *           voxel centred at ((x - d/2) apix, (y - d/2) apix, (z - d/2) apix) A;
+ *           16-byte aligned.
+ * Gaussians with a zero scale, a zero quaternion (unless no_rotation) or
+ * rho <= 0 contribute nothing.  Slices run in batches of max_B through the
+ * projection scratch, so the call ends the state kept for gem_backward
+ * (a later gem_backward returns GEM_ESTATE).  Pair lists that overflow
+ * max_pairs are reported by gem_status (GEM_ECAPACITY).  Asynchronous.
+ * Errors: GEM_EINVAL, GEM_ECUDA. */
+int gem_query(gem_ctx *ctx, const float *params, int64_t M, float tau, float *vol);
 
 /* k nearest neighbours of the Gaussian centres (Sec. 4, Design Choices of
  * 3DGS for cryo-EM: the isotropic-scaling ablation takes s_j = the distance

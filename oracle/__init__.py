@@ -62,6 +62,8 @@ def _load():
                 "gem_oracle_ctf_apply": (None, [I, I, P, P, P]),
                 "gem_oracle_loss": (D, [I, I, P, P, P, P, P, P]),
                 "gem_oracle_grad": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
+                "gem_oracle_query": (None, [I, D, D, I, L, P, P]),
+                "gem_oracle_query_voxels": (None, [I, D, D, I, L, P, L, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -217,6 +219,26 @@ def forward_loss(params, R, t, hfull, images, d, apix, tau, norm_mode: int = 0, 
     """L(theta) through the whole path; used for central differences."""
     proj = project(params, R, t, d, apix, tau, norm_mode, no_rotation, isotropic)
     return loss(hfull, proj, images)[0]
+
+
+def query(params, d: int, apix: float, tau: float, norm_mode: int = 0, no_rotation=False,
+          isotropic=False) -> np.ndarray:
+    """Eq. query on the d^3 voxel grid, vol[z][y][x], terms above tau only."""
+    params = constrained(params, no_rotation, isotropic)
+    vol = np.zeros((d, d, d))
+    _load().gem_oracle_query(d, apix, tau, norm_mode, params.shape[0], _ptr(params), _ptr(vol))
+    return vol
+
+
+def query_voxels(params, d, apix, tau, vox, norm_mode: int = 0, no_rotation=False,
+                 isotropic=False) -> np.ndarray:
+    """Eq. query at flat voxel indices vox = (z d + y) d + x."""
+    params = constrained(params, no_rotation, isotropic)
+    vox = np.ascontiguousarray(np.asarray(vox, dtype=np.int64))
+    out = np.zeros(vox.shape[0])
+    _load().gem_oracle_query_voxels(d, apix, tau, norm_mode, params.shape[0], _ptr(params),
+                                    vox.shape[0], _ptr(vox), _ptr(out))
+    return out
 
 
 def nn_distance(pos, k: int):

@@ -516,3 +516,89 @@ void gem_oracle_grad(int d, double apix, double tau, int norm_mode, int64_t M,
     for (int m = 0; m < NPAR; ++m) grad[i * NPAR + m] = acc[m];
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. query: density of the Gaussians on the voxel grid                     */
+/* ------------------------------------------------------------------------ */
+
+/* The 3D Gaussian of Eq. G: mean, precision Sigma^-1 (cofactors over the
+ * determinant of Sigma = R S S^T R^T), amplitude.  norm_mode 1: amplitude rho
+ * (a peak density, Eq. G as printed); norm_mode 0: rho / ((2 pi)^3/2
+ * |Sigma|^1/2), the normalised density of mass rho whose line integral is the
+ * Eq. render term.  Returns 0 when the Gaussian contributes nothing. */
+static int gauss3(const double *theta, int norm_mode, double mean[3], double P[3][3],
+                  double *amp) {
+  const double *s = theta + 3, *q = theta + 6;
+  double rho = theta[10];
+  double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(qn > 0.0) || !isfinite(qn) || !(rho > 0.0)) return 0;
+  double w = q[0] / qn, v[3] = {q[1] / qn, q[2] / qn, q[3] / qn};
+  double Rq[3][3], S[3][3];
+  rot_of_unit_quat(w, v, Rq);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0;
+      for (int k = 0; k < 3; ++k) acc += Rq[a][k] * s[k] * s[k] * Rq[b][k];
+      S[a][b] = acc;
+    }
+  double C[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      int a1 = (a + 1) % 3, a2 = (a + 2) % 3, b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+      C[a][b] = S[a1][b1] * S[a2][b2] - S[a1][b2] * S[a2][b1];
+    }
+  double det = S[0][0] * C[0][0] + S[0][1] * C[0][1] + S[0][2] * C[0][2];
+  if (!(det > 0.0) || !isfinite(det)) return 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) P[a][b] = C[b][a] / det;
+  for (int a = 0; a < 3; ++a) mean[a] = theta[a];
+  *amp = norm_mode == 0 ? rho / (pow(2.0 * PI, 1.5) * sqrt(det)) : rho;
+  return 1;
+}
+
+static double voxel_value(const double mean[3], const double P[3][3], double amp, double x,
+                          double y, double z) {
+  double dv[3] = {x - mean[0], y - mean[1], z - mean[2]};
+  double qf = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) qf += dv[a] * P[a][b] * dv[b];
+  return amp * exp(-0.5 * qf);
+}
+
+/* Density at selected flat voxel indices vox = (z d + y) d + x: every
+ * Gaussian, terms above tau only (Eq. accu applied to the 3D value). */
+void gem_oracle_query_voxels(int d, double apix, double tau, int norm_mode, int64_t M,
+                             const double *params, int64_t n, const int64_t *vox, double *out) {
+  double(*mean)[3] = malloc(sizeof(double[3]) * (size_t)M);
+  double(*P)[3][3] = malloc(sizeof(double[3][3]) * (size_t)M);
+  double *amp = malloc(sizeof(double) * (size_t)M);
+  int *ok = malloc(sizeof(int) * (size_t)M);
+  for (int64_t j = 0; j < M; ++j) ok[j] = gauss3(params + j * NPAR, norm_mode, mean[j], P[j], &amp[j]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t v = vox[i];
+    int x = (int)(v % d), y = (int)((v / d) % d), z = (int)(v / ((int64_t)d * d));
+    double X = pix_coord(x, d, apix), Y = pix_coord(y, d, apix), Z = pix_coord(z, d, apix);
+    double acc = 0;
+    for (int64_t j = 0; j < M; ++j) {
+      if (!ok[j]) continue;
+      double val = voxel_value(mean[j], P[j], amp[j], X, Y, Z);
+      if (val > tau) acc += val;
+    }
+    out[i] = acc;
+  }
+  free(mean);
+  free(P);
+  free(amp);
+  free(ok);
+}
+
+/* The whole d^3 grid, vol[z][y][x]. */
+void gem_oracle_query(int d, double apix, double tau, int norm_mode, int64_t M,
+                      const double *params, double *vol) {
+  int64_t n = (int64_t)d * d * d;
+  int64_t *vox = malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) vox[i] = i;
+  gem_oracle_query_voxels(d, apix, tau, norm_mode, M, params, n, vox, vol);
+  free(vox);
+}

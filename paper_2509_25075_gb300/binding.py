@@ -74,6 +74,7 @@ SIGNATURES = {
     "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "gem_ctf_loss_static": (ctypes.c_int, [_I32, _F, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gem_nn_distance": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
+    "gem_query": (ctypes.c_int, [_P, _P, _I64, _F, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
@@ -256,6 +257,17 @@ class Context:
         k, e = ctypes.c_int64(), ctypes.c_int64()
         self._rc(self.lib.gem_pair_stats(self.h, ctypes.byref(k), ctypes.byref(e)))
         return int(k.value), int(e.value)
+
+    def gem_query(self, params, tau: float = 0.0, vol=None):
+        """Density on the d^3 voxel grid (Eq. query) -> vol [d][d][d] float32."""
+        M, d = params.shape[0], self.d
+        _check(params, "params", (M, NPAR))
+        if vol is None:
+            vol = torch.empty(d, d, d, dtype=torch.float32, device=params.device)
+        _check(vol, "vol", (d, d, d))
+        self._rc(self.lib.gem_query(self.h, _ptr(params), M, tau, _ptr(vol)))
+        self.M = self.B = None
+        return vol
 
     def gem_nn_distance(self, params, k: int, dist=None, idx=None):
         """-> (dist [M][k] float32, idx [M][k] int32) of the centres' k nearest neighbours."""

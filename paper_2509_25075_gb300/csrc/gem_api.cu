@@ -40,6 +40,7 @@ struct gem_ctx {
   int *status = nullptr;
   unsigned long long *kept = nullptr;
   KnnScratch knn{};
+  QueryPrep *qp = nullptr;
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -48,6 +49,14 @@ struct gem_ctx {
   int64_t launches[GEM_NSTAGES] = {};
   // state of the last projection
   bool have_proj = false;
+  // tile lists of the last gem_project (bins_of_proj) or of the last slice
+  // batch of gem_query, binned for M = bins_M Gaussians, B = bins_B images
+  // with threshold bins_l2tau
+  bool have_bins = false;
+  bool bins_of_proj = false;
+  int64_t bins_M = 0;
+  int bins_B = 0;
+  float bins_l2tau = 0.f;
   bool have_dproj = false;
   const float *params = nullptr;
   const float *R = nullptr;
@@ -196,7 +205,8 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
        alloc(c, &c->knn.cell, g.max_M) && alloc(c, &c->knn.cnt, c->knn.cap) &&
        alloc(c, &c->knn.start, c->knn.cap + 1) && alloc(c, &c->knn.fill, c->knn.cap) &&
        alloc(c, &c->knn.order, g.max_M) &&
-       alloc(c, &c->knn.bsum, (size_t)knn_scan_blocks(c->knn.cap) + 1);
+       alloc(c, &c->knn.bsum, (size_t)knn_scan_blocks(c->knn.cap) + 1) &&
+       alloc(c, &c->qp, g.max_M);
   if (!ok) {
     snprintf(g_create_err, sizeof(g_create_err), "device allocation failed");
     gem_destroy(c);
@@ -303,9 +313,15 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   const uint32_t *perm = nullptr;
   {
     StageScope sc(c, GEM_STAGE_BIN, g.zsort ? 10 : 4);
+    c->have_bins = false;
     if ((e = launch_bin(c->rec, c->bin.key, M, B, g.d, c->l2tau, g.zsort, c->bin, &perm,
                         c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "bin");
+    c->have_bins = true;
+    c->bins_of_proj = true;
+    c->bins_M = M;
+    c->bins_B = B;
+    c->bins_l2tau = c->l2tau;
   }
   {
     StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
@@ -324,6 +340,7 @@ int gem_project_dense(gem_ctx *c, const float *params, int64_t M, int32_t B, con
   c->have_proj = false;
   c->have_dproj = false;
   if ((rc = prep(c, params, M, B, R, t))) return rc;
+  c->have_bins = false;  // the records changed; any tile lists are stale
   cudaError_t e;
   StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
   if ((e = launch_dense_fwd(c->rec, M, B, c->cfg.d, c->l2tau, proj, c->stream)) != cudaSuccess)
@@ -356,6 +373,8 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
   if (!dproj || !grad) return fail(c, GEM_EINVAL, "null dproj or grad");
   if (!aligned16(dproj)) return fail(c, GEM_EINVAL, "dproj must be 16-byte aligned");
   if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection to differentiate");
+  if (!dense && !(c->have_bins && c->bins_of_proj))
+    return fail(c, GEM_ESTATE, "the last projection was dense: no tile lists to differentiate");
   const gem_config &g = c->cfg;
   cudaError_t e;
   size_t mbytes = (size_t)c->B * c->M * 6 * sizeof(float);
@@ -408,10 +427,10 @@ int gem_backward(gem_ctx *c, float *grad) {
 
 int gem_pair_count(gem_ctx *c, int64_t *n) {
   if (!c || !n) return GEM_EINVAL;
-  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
+  if (!c->have_bins) return fail(c, GEM_ESTATE, "no tile lists yet");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
-  e = cudaMemcpy(n, c->bin.tile_start + (int64_t)c->B * c->T, sizeof(int64_t),
+  e = cudaMemcpy(n, c->bin.tile_start + (int64_t)c->bins_B * c->T, sizeof(int64_t),
                  cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair count read");
   return GEM_OK;
@@ -426,7 +445,7 @@ int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t li
   if (list_cap < n) return fail(c, GEM_EINVAL, "list_cap %lld < pair count %lld",
                                 (long long)list_cap, (long long)n);
   cudaError_t e;
-  size_t ts = ((size_t)c->B * c->T + 1) * sizeof(int64_t);
+  size_t ts = ((size_t)c->bins_B * c->T + 1) * sizeof(int64_t);
   if ((e = cudaMemcpy(tile_start, c->bin.tile_start, ts, cudaMemcpyDeviceToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(list, c->bin.list, (size_t)n * sizeof(uint32_t),
@@ -448,13 +467,14 @@ int gem_inspect_records(gem_ctx *c, float *out) {
 
 int gem_pair_stats(gem_ctx *c, int64_t *kept, int64_t *evaluated) {
   if (!c || !kept) return GEM_EINVAL;
-  if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
+  if (!c->have_bins) return fail(c, GEM_ESTATE, "no tile lists yet");
   const gem_config &g = c->cfg;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->kept, 0, 2 * sizeof(unsigned long long), c->stream)) !=
           cudaSuccess ||
-      (e = launch_count_kept(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, c->M, c->B,
-                             g.d, c->l2tau, c->kept, c->stream)) != cudaSuccess ||
+      (e = launch_count_kept(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap,
+                             c->bins_M, c->bins_B, g.d, c->bins_l2tau, c->kept, c->stream)) !=
+          cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "pair count");
   unsigned long long h[2] = {0, 0};
@@ -494,6 +514,45 @@ int gem_timing_read(gem_ctx *c, float *ms, int64_t *launches) {
     if (launches) launches[i] = c->launches[i];
     c->recorded[i] = false;
     c->launches[i] = 0;
+  }
+  return GEM_OK;
+}
+
+int gem_query(gem_ctx *c, const float *params, int64_t M, float tau, float *vol) {
+  if (!c) return GEM_EINVAL;
+  if (!params || !vol) return fail(c, GEM_EINVAL, "null params or vol");
+  if (!aligned16(vol)) return fail(c, GEM_EINVAL, "vol must be 16-byte aligned");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  if (!(tau >= 0.f) || !isfinite(tau)) return fail(c, GEM_EINVAL, "tau must be finite and >= 0");
+  const gem_config &g = c->cfg;
+  // the slices reuse the projection scratch: the backward state is gone
+  c->have_proj = false;
+  c->have_dproj = false;
+  c->have_bins = false;
+  const float l2tau = tau > 0.f ? log2f(tau) : -INFINITY;
+  cudaError_t e;
+  if ((e = launch_query_prep(params, M, g.norm_mode, shape_flags(g), c->qp, c->stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "query prep");
+  const size_t slice = (size_t)g.d * g.d;
+  for (int k0 = 0; k0 < g.d; k0 += g.max_B) {
+    const int ns = g.d - k0 < g.max_B ? g.d - k0 : g.max_B;
+    const uint32_t *perm = nullptr;
+    if ((e = launch_slice_prep(c->qp, M, k0, ns, g.apix, g.d, l2tau, c->rec, c->stream)) !=
+            cudaSuccess ||
+        (e = launch_bin(c->rec, c->bin.key, M, ns, g.d, l2tau, 0, c->bin, &perm, c->stream)) !=
+            cudaSuccess ||
+        (e = launch_raster_fwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap,
+                               M, ns, g.d, l2tau, vol + (size_t)k0 * slice, c->stream)) !=
+            cudaSuccess)
+      return cuda_fail(c, e, "query");
+    c->have_bins = true;
+    c->bins_of_proj = false;
+    c->bins_M = M;
+    c->bins_B = ns;
+    c->bins_l2tau = l2tau;
   }
   return GEM_OK;
 }

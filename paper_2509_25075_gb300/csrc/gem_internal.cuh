@@ -250,6 +250,23 @@ cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t 
                                    const float *R, const float *t, float apix, int d, float *out,
                                    cudaStream_t st);
 
+// gem_query.cu
+// Per-Gaussian quantities of the density query (48 B): centre, xy block of
+// Sigma^-1 (1/Angstrom^2), Sigma_xz / Sigma_zz, Sigma_yz / Sigma_zz,
+// 1 / Sigma_zz, log2 of the 3D amplitude, valid flag.
+struct __align__(16) QueryPrep {
+  float p[3];
+  float pxx, pxy, pyy;
+  float mx, my, hz;
+  float l2A;
+  float valid;
+  float pad;
+};
+cudaError_t launch_query_prep(const float *params, int64_t M, int norm_mode, int shape,
+                              QueryPrep *qp, cudaStream_t st);
+cudaError_t launch_slice_prep(const QueryPrep *qp, int64_t M, int k0, int nslice, float apix,
+                              int d, float l2tau, Rec *rec, cudaStream_t st);
+
 // gem_knn.cu
 struct KnnGrid {
   float lo[3];  // corner of the centres' bounding box

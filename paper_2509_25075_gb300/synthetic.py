@@ -59,6 +59,14 @@ class Workload:
         s_min = self.s_lo * self.apix
         return float(np.float32(1e-4 * 1.5 / (2.0 * math.pi * s_min * s_min)))
 
+    @property
+    def tau_query(self) -> float:
+        """Threshold of the density query (Eq. query with Eq. accu applied to
+        the 3D value): 1e-4 of the largest possible mode-0 peak density
+        rho_max / ((2 pi)^3/2 s_min^3), rounded to float32."""
+        s_min = self.s_lo * self.apix
+        return float(np.float32(1e-4 * 1.5 / ((2.0 * math.pi) ** 1.5 * s_min ** 3)))
+
     def as_config(self) -> dict:
         c = asdict(self)
         c["tau"] = self.tau

@@ -81,3 +81,17 @@ def test_capacity_overflow_is_reported_not_faulted():
     full.gem_project(*args, proj)
     assert full.gem_status() == binding.GEM_OK
     assert torch.equal(proj, proj_full)
+
+
+def test_tiled_backward_after_dense_projection_is_a_state_error():
+    args, _ = _inputs()
+    ctx = gt.context(W)
+    proj = torch.empty(W.B, W.d, W.d, device=gt.DEV)
+    ctx.gem_project(*args, proj)
+    ctx.gem_project_dense(*args, proj)  # replaces the records; its lists are stale
+    grad = torch.empty(W.M, 11, device=gt.DEV)
+    with pytest.raises(binding.GemError) as ei:
+        ctx.gem_project_backward(torch.zeros_like(proj), grad)
+    assert ei.value.code == binding.GEM_ESTATE
+    ctx.gem_project_backward_dense(torch.zeros_like(proj), grad)
+    assert torch.count_nonzero(grad).item() == 0
