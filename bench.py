@@ -52,6 +52,18 @@ CAPTURED_TRAFFIC = {
 }
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth of this GPU pool (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "6.8 TB/s (of fallback)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_NOTE = _hbm_peak()
+
+
 def raster_source_hash() -> str:
     """Hash of the rasterisers' source: gem_raster.cu and the device helpers
     and types of gem_internal.cuh (the part before its launcher list)."""
@@ -422,6 +434,30 @@ def main():
         query = {"ms": q_ms, "voxels_per_s": w.d ** 3 / (q_ms / 1e3), "grid": w.d, "M": w.M, "tau": tq,
                  "slice_batches": nbatch, "gpu_launches_per_call": 1 + 6 * nbatch,
                  "l2": "flushed before each call (256 MB write)"}
+        # Fourier shell correlation of the map against the map of perturbed
+        # Gaussians (the two half-maps of Eq. fsc)
+        vol2 = torch.empty_like(vol)
+        p2 = D["params"].clone()
+        p2[:, 0:3] += 0.3 * w.apix * torch.randn(w.M, 3, device=dev, generator=torch.Generator(dev).manual_seed(5))
+        ctx.gem_query(p2, tq, vol2)
+        fsc_out = None
+        for _ in range(3):
+            fsc_out = ctx.gem_fsc(vol, vol2)
+        torch.cuda.synchronize()
+        fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nq)]
+        for i in range(nq):
+            flush.zero_()
+            fe[i][0].record(stream)
+            ctx.gem_fsc(vol, vol2)
+            fe[i][1].record(stream)
+        torch.cuda.synchronize()
+        f_ms = sum(a.elapsed_time(b) for a, b in fe) / nq
+        f_bytes = 64 * w.d ** 3  # 3 FFT passes (read + write d^3 complex) and the shell pass (2 reads)
+        f_gbs = f_bytes / (f_ms / 1e3) / 1e9
+        query["fsc"] = {"ms": f_ms, "resolution_A": float(fsc_out[2].item()), "gpu_launches_per_call": 5,
+                        "roofline": {"bound": "hbm", "achieved": f_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                     "frac": f_gbs / HBM_PEAK_GBS, "algorithmic_bytes": f_bytes,
+                                     "peak_note": HBM_PEAK_NOTE}}
         if nbatch == 1:
             qk, qv = ctx.gem_pair_stats()
             qa = qk / (q_ms / 1e3) / 1e9

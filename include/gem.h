@@ -221,6 +221,29 @@ int gem_pair_stats(gem_ctx *ctx, int64_t *kept, int64_t *evaluated);
  * Errors: GEM_EINVAL, GEM_ECUDA. */
 int gem_query(gem_ctx *ctx, const float *params, int64_t M, float tau, float *vol);
 
+/* Fourier shell correlation of two maps (Eq. fsc; Sec. 4, Gold-Standard
+ * Fourier Shell Correlation) on the context's d x d x d grid:
+ *   FSC(i) = Re sum_{k in shell i} F1(k) F2(k)^* / sqrt(sum |F1|^2 . sum |F2|^2),
+ * F1, F2 the 3D DFTs of the maps, shell i = the frequencies whose signed
+ * DFT indices k have round(|k|) = i, i = 0 .. d/2 (the corners beyond the
+ * Nyquist sphere are not used).  Shell i is the resolution d apix / i A.
+ *   map1, map2  device float [d][d][d] (e.g. two gem_query outputs);
+ *   threshold   the FSC level whose crossing sets the resolution (0.143 in
+ *               the paper), in (-1, 1);
+ *   fsc         device double [d/2 + 1];
+ *   sums        device double [3][d/2 + 1] or NULL: per shell the numerator
+ *               and the two power sums;
+ *   resolution  device double [1] or NULL: d apix / k*, k* the first
+ *               crossing below the threshold (first shell i >= 1 with
+ *               FSC < threshold, interpolated linearly from shell i - 1);
+ *               2 apix (Nyquist) when the curve never crosses.
+ * A shell without power has FSC 0.  The first call allocates 16 d^3 bytes
+ * of scratch that the context keeps.  Asynchronous.  The sums are reduced
+ * in double with shared-memory atomics: not bitwise repeatable, ~1e-15.
+ * Errors: GEM_EINVAL, GEM_ENOMEM, GEM_ECUDA. */
+int gem_fsc(gem_ctx *ctx, const float *map1, const float *map2, float threshold, double *fsc,
+            double *sums, double *resolution);
+
 /* k nearest neighbours of the Gaussian centres (Sec. 4, Design Choices of
  * 3DGS for cryo-EM: the isotropic-scaling ablation takes s_j = the distance
  * of Gaussian j to its nearest neighbour; also a scale initialisation).

@@ -274,3 +274,48 @@ def nn_distance(pos, k: int):
             dist[i, :n] = np.sqrt(d2[r][order[:n]])
             idx[i, :n] = order[:n]
     return dist, idx
+
+
+def fsc_shell_sums(X1, X2, nshell: int | None = None):
+    """Per-shell sums of Eq. fsc: (Re sum F1 F2^*, sum |F1|^2, sum |F2|^2),
+    F = the 3D DFT (numpy.fft.fftn) of each real map, shell i = frequencies
+    whose signed DFT indices k have round(|k|) = i.  nshell defaults to every
+    shell that holds a frequency (the cube's corners included)."""
+    X1, X2 = _f64(X1), _f64(X2)
+    d = X1.shape[0]
+    F1, F2 = np.fft.fftn(X1), np.fft.fftn(X2)
+    k = np.fft.fftfreq(d) * d
+    k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
+    shell = np.floor(np.sqrt(k2) + 0.5).astype(np.int64).ravel()
+    n = int(shell.max()) + 1 if nshell is None else nshell
+    keep = shell < n
+    num = np.bincount(shell[keep], weights=np.real(F1 * np.conj(F2)).ravel()[keep], minlength=n)
+    p1 = np.bincount(shell[keep], weights=(np.abs(F1) ** 2).ravel()[keep], minlength=n)
+    p2 = np.bincount(shell[keep], weights=(np.abs(F2) ** 2).ravel()[keep], minlength=n)
+    return num, p1, p2
+
+
+def fsc_crossing(curve, d: int, apix: float, threshold: float = 0.143) -> float:
+    """Resolution (Angstrom) where the FSC curve first drops below the
+    threshold (Sec. 4, GSFSC): the first shell i >= 1 with FSC(i) < threshold,
+    the crossing interpolated linearly between shells i-1 and i (clamped to
+    that interval), resolution d apix / k*.  A curve that never drops gives
+    the last shell."""
+    c = np.asarray(curve, dtype=np.float64)
+    kstar = float(len(c) - 1)
+    for i in range(1, len(c)):
+        if c[i] < threshold:
+            a, b = c[i - 1], c[i]
+            frac = (a - threshold) / (a - b) if a > b else 0.0
+            kstar = (i - 1) + min(max(frac, 0.0), 1.0)
+            break
+    return d * apix / kstar if kstar > 0 else float("inf")
+
+
+def fsc(X1, X2, apix: float, threshold: float = 0.143):
+    """Eq. fsc over the shells 0 .. d/2 -> (fsc, (num, p1, p2), resolution)."""
+    d = np.asarray(X1).shape[0]
+    num, p1, p2 = fsc_shell_sums(X1, X2, d // 2 + 1)
+    den = np.sqrt(p1 * p2)
+    curve = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    return curve, (num, p1, p2), fsc_crossing(curve, d, apix, threshold)

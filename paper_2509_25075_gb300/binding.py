@@ -75,6 +75,7 @@ SIGNATURES = {
     "gem_ctf_loss_static": (ctypes.c_int, [_I32, _F, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gem_nn_distance": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
     "gem_query": (ctypes.c_int, [_P, _P, _I64, _F, _P]),
+    "gem_fsc": (ctypes.c_int, [_P, _P, _P, _F, _P, _P, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
@@ -268,6 +269,19 @@ class Context:
         self._rc(self.lib.gem_query(self.h, _ptr(params), M, tau, _ptr(vol)))
         self.M = self.B = None
         return vol
+
+    def gem_fsc(self, map1, map2, threshold: float = 0.143):
+        """-> (fsc [d/2+1], sums [3][d/2+1], resolution [1]) as float64 device tensors."""
+        d = self.d
+        _check(map1, "map1", (d, d, d))
+        _check(map2, "map2", (d, d, d))
+        nsh = d // 2 + 1
+        fsc = torch.empty(nsh, dtype=torch.float64, device=map1.device)
+        sums = torch.empty(3, nsh, dtype=torch.float64, device=map1.device)
+        res = torch.empty(1, dtype=torch.float64, device=map1.device)
+        self._rc(self.lib.gem_fsc(self.h, _ptr(map1), _ptr(map2), threshold, _ptr(fsc), _ptr(sums),
+                                  _ptr(res)))
+        return fsc, sums, res
 
     def gem_nn_distance(self, params, k: int, dist=None, idx=None):
         """-> (dist [M][k] float32, idx [M][k] int32) of the centres' k nearest neighbours."""

@@ -41,6 +41,9 @@ struct gem_ctx {
   unsigned long long *kept = nullptr;
   KnnScratch knn{};
   QueryPrep *qp = nullptr;
+  // FSC scratch, allocated by the first gem_fsc: two d^3 complex volumes
+  float2 *fscP = nullptr, *fscQ = nullptr;
+  double *fsc_part = nullptr;
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -554,6 +557,27 @@ int gem_query(gem_ctx *c, const float *params, int64_t M, float tau, float *vol)
     c->bins_B = ns;
     c->bins_l2tau = l2tau;
   }
+  return GEM_OK;
+}
+
+int gem_fsc(gem_ctx *c, const float *map1, const float *map2, float threshold, double *fsc,
+            double *sums, double *resolution) {
+  if (!c) return GEM_EINVAL;
+  if (!map1 || !map2 || !fsc) return fail(c, GEM_EINVAL, "null map or fsc");
+  if (!(threshold > -1.f && threshold < 1.f))
+    return fail(c, GEM_EINVAL, "threshold must lie in (-1, 1)");
+  const int d = c->cfg.d;
+  if (!c->fscP) {
+    const size_t n = (size_t)d * d * d;
+    if (!alloc(c, &c->fscP, n) || !alloc(c, &c->fscQ, n) ||
+        !alloc(c, &c->fsc_part, (size_t)fsc_partial_count(d)))
+      return fail(c, GEM_ENOMEM, "FSC scratch (%zu bytes) allocation failed", 16 * n);
+    cudaError_t e = fsc_configure(d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fsc configure");
+  }
+  cudaError_t e = launch_fsc(d, c->cfg.apix, threshold, c->plan, c->tw, map1, map2, c->fscP,
+                             c->fscQ, c->fsc_part, fsc, sums, resolution, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fsc");
   return GEM_OK;
 }
 

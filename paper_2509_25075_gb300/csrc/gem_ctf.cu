@@ -22,6 +22,7 @@
 // FFTs are radix-4/2/3 Stockham transforms in shared memory (d = 2^a 3^b).
 #include <math.h>
 
+#include "gem_fft.cuh"
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -50,86 +51,12 @@ bool fft_plan(int n, FftPlan &p) {
   return m == 1;
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// One radix-R Stockham stage on every line (kLines lines of length n).
-// Butterfly jj of a line reads elements jj + r n/R, twiddles them by
-// W^(r k n/(Ns R)), k = jj mod Ns, and writes (jj / Ns) Ns R + k + r Ns.
-template <int R>
-__device__ __forceinline__ void fft_stage(const float2 *__restrict__ src, float2 *__restrict__ dst,
-                                          int nl, int n, int Ns, const float2 *__restrict__ tw) {
-  const int nb = n / R;
-  const int tws = n / (Ns * R);
-  const int total = nl * nb;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx / nb;
-    const int jj = idx - line * nb;
-    const float2 *in = src + line * n;
-    float2 *out = dst + line * n;
-    const int k = jj % Ns;
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[jj + r * nb];
-#pragma unroll
-    for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
-    if (R == 4) {
-      float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-      float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-      float2 a2 = make_float2(v[1].x + v[3 % R].x, v[1].y + v[3 % R].y);
-      float2 a3 = make_float2(v[1].y - v[3 % R].y, v[3 % R].x - v[1].x);  // (v1 - v3) (-i)
-      v[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
-      v[2 % R] = make_float2(a0.x - a2.x, a0.y - a2.y);
-      v[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
-      v[3 % R] = make_float2(a1.x - a3.x, a1.y - a3.y);
-    } else if (R == 2) {
-      float2 a0 = v[0];
-      v[0] = make_float2(a0.x + v[1].x, a0.y + v[1].y);
-      v[1] = make_float2(a0.x - v[1].x, a0.y - v[1].y);
-    } else {  // R == 3
-      const float h = 0.8660254037844386f;  // sqrt(3)/2
-      float2 t1 = make_float2(v[1].x + v[2 % R].x, v[1].y + v[2 % R].y);
-      float2 t2 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
-      float2 t3 = make_float2(h * (v[1].y - v[2 % R].y), -h * (v[1].x - v[2 % R].x));
-      v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
-      v[1] = make_float2(t2.x + t3.x, t2.y + t3.y);
-      v[2 % R] = make_float2(t2.x - t3.x, t2.y - t3.y);
-    }
-    const int obase = (jj / Ns) * Ns * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) out[obase + r * Ns] = v[r];
-  }
-}
-
-// Forward (e^{-2 pi i}) FFT of nl lines of length n, src -> dst -> src ...;
-// returns the buffer holding the result.  tw[m] = e^{-2 pi i m / n}.
-__device__ float2 *fft_lines(float2 *src, float2 *dst, int nl, const FftPlan &pl,
-                             const float2 *__restrict__ tw) {
-  const int n = pl.n;
-  int Ns = 1;
-  for (int s = 0; s < pl.nst; ++s) {
-    const unsigned c = (pl.code >> (2 * s)) & 3u;
-    const int R = c == 2 ? 4 : (c == 1 ? 3 : 2);
-    if (R == 4)
-      fft_stage<4>(src, dst, nl, n, Ns, tw);
-    else if (R == 2)
-      fft_stage<2>(src, dst, nl, n, Ns, tw);
-    else
-      fft_stage<3>(src, dst, nl, n, Ns, tw);
-    __syncthreads();
-    float2 *tmp = src;
-    src = dst;
-    dst = tmp;
-    Ns *= R;
-  }
-  return src;
-}
-
 constexpr int kLines = 16;  // lines per CTA in every pass
 constexpr int kCtfThreads = 256;
 
-static size_t ctf_smem(int d) { return (size_t)(2 * kLines * d + d) * sizeof(float2); }
+// line stride in shared memory: one element of padding per line
+__host__ __device__ constexpr int ctf_ls(int d) { return d + 1; }
+static size_t ctf_smem(int d) { return (size_t)(2 * kLines * ctf_ls(d) + d) * sizeof(float2); }
 
 __device__ __forceinline__ void load_twiddles(float2 *tw_s, const float2 *__restrict__ tw,
                                               int n) {
@@ -142,18 +69,22 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass1_kernel(
     const float2 *__restrict__ tw, float2 *__restrict__ Z) {
   extern __shared__ float2 sm[];
   const int d = pl.n;
-  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int ls = ctf_ls(d);
+  float2 *a = sm, *bb = sm + kLines * ls, *tws = sm + 2 * kLines * ls;
   const int y0 = blockIdx.x * kLines, b = blockIdx.y;
   load_twiddles(tws, tw, d);
   const float *pr = proj + ((int64_t)b * d + y0) * d;
   const float *im = images + ((int64_t)b * d + y0) * d;
-  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) a[i] = make_float2(pr[i], im[i]);
+  for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
+    const int l = i / d, x = i - l * d;
+    a[l * ls + x] = make_float2(pr[i], im[i]);
+  }
   __syncthreads();
-  float2 *res = fft_lines(a, bb, kLines, pl, tws);
+  float2 *res = fft_lines(a, bb, kLines, pl, tws, ls);
   float2 *zb = Z + (int64_t)b * d * d;
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
     int l = i % kLines, kx = i / kLines;
-    zb[(int64_t)kx * d + y0 + l] = res[l * d + kx];
+    zb[(int64_t)kx * d + y0 + l] = res[l * ls + kx];
   }
 }
 
@@ -258,7 +189,8 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   __shared__ CtfConst cc;
   __shared__ double red[kCtfThreads / 32];
   const int d = pl.n, hd = d / 2;
-  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int ls = ctf_ls(d);
+  float2 *a = sm, *bb = sm + kLines * ls, *tws = sm + 2 * kLines * ls;
   const int blk = blockIdx.x, b = blockIdx.y;
   load_twiddles(tws, tw, d);
   if (ctf_params && threadIdx.x == 0) cc = ctf_const(ctf_params + 8 * b, d, apix);
@@ -272,10 +204,10 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
       int kx = i < 8 ? kx1 : (d - kx1) % d;
       v = zb[(int64_t)kx * d + y];
     }
-    a[idx] = v;
+    a[i * ls + y] = v;
   }
   __syncthreads();
-  float2 *L = fft_lines(a, bb, kLines, pl, tws);
+  float2 *L = fft_lines(a, bb, kLines, pl, tws, ls);
   // combine: thread per (pair i, ky)
   float lsum = 0.f;
   for (int idx = threadIdx.x; idx < 8 * d; idx += blockDim.x) {
@@ -285,8 +217,8 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     bool self = (kx == 0 || kx == hd);
     if (self && ky > hd) continue;
     int mky = (d - ky) % d;
-    float2 *l1 = L + i * d;
-    float2 *l2 = self ? l1 : L + (8 + i) * d;
+    float2 *l1 = L + i * ls;
+    float2 *l2 = self ? l1 : L + (8 + i) * ls;
     float2 z1 = l1[ky], z2 = l2[mky];
     // X = (z1 + conj z2) / 2,  Y = (z1 - conj z2) / (2 i)
     float2 X = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
@@ -318,9 +250,9 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     l2[mky] = make_float2(Wm.x, -Wm.y);
   }
   // block reduction of the loss partial in float64
-  double ls = (double)lsum;
-  for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ls;
+  double lw = (double)lsum;
+  for (int o = 16; o > 0; o >>= 1) lw += __shfl_xor_sync(0xffffffffu, lw, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lw;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -329,7 +261,7 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   }
   // inverse along y (conjugated forward transform)
   float2 *other = (L == a) ? bb : a;
-  float2 *R2 = fft_lines(L, other, kLines, pl, tws);
+  float2 *R2 = fft_lines(L, other, kLines, pl, tws, ls);
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
     int i = idx / d, y = idx - i * d;
     int kx1 = 8 * blk + (i & 7);
@@ -337,7 +269,7 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     bool self = (kx1 == 0 || kx1 == hd);
     if (i >= 8 && self) continue;
     int kx = i < 8 ? kx1 : d - kx1;
-    float2 v = R2[idx];
+    float2 v = R2[i * ls + y];
     zb[(int64_t)kx * d + y] = make_float2(v.x, -v.y);
   }
 }
@@ -349,20 +281,22 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
     float gscale, float *__restrict__ pred, float *__restrict__ dproj) {
   extern __shared__ float2 sm[];
   const int d = pl.n;
-  float2 *a = sm, *bb = sm + kLines * d, *tws = sm + 2 * kLines * d;
+  const int ls = ctf_ls(d);
+  float2 *a = sm, *bb = sm + kLines * ls, *tws = sm + 2 * kLines * ls;
   const int y0 = blockIdx.x * kLines, b = blockIdx.y;
   load_twiddles(tws, tw, d);
   const float2 *zb = Z + (int64_t)b * d * d;
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
     int l = i % kLines, kx = i / kLines;
     float2 v = zb[(int64_t)kx * d + y0 + l];
-    a[l * d + kx] = make_float2(v.x, -v.y);
+    a[l * ls + kx] = make_float2(v.x, -v.y);
   }
   __syncthreads();
-  float2 *res = fft_lines(a, bb, kLines, pl, tws);
+  float2 *res = fft_lines(a, bb, kLines, pl, tws, ls);
   int64_t off = ((int64_t)b * d + y0) * d;
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
-    float2 v = res[i];
+    const int l = i / d, x = i - l * d;
+    float2 v = res[l * ls + x];
     if (pred) pred[off + i] = v.x * inv_n2;
     if (dproj) dproj[off + i] = -v.y * gscale;
   }

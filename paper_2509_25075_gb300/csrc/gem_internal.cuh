@@ -336,6 +336,13 @@ struct FftPlan {
 bool fft_plan(int n, FftPlan &p);
 cudaError_t ctf_configure(int d);
 size_t ctf_partials(int d);
+// gem_fsc.cu
+cudaError_t fsc_configure(int d);
+int fsc_partial_count(int d);  // doubles of block partial sums
+cudaError_t launch_fsc(int d, float apix, float thr, const FftPlan &plan, const float2 *tw,
+                       const float *X1, const float *X2, float2 *P, float2 *Q, double *part,
+                       double *fsc, double *sums, double *resolution, cudaStream_t st);
+
 cudaError_t launch_ctf_loss(int d, int B, float apix, const FftPlan &plan, const float2 *tw,
                             const float *proj, const float *ctf, const float *ctf_params,
                             const float *images, float2 *Z, double *lossp, float *pred,
