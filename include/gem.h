@@ -263,6 +263,41 @@ int gem_fsc(gem_ctx *ctx, const float *map1, const float *map2, float threshold,
 int gem_nn_distance(gem_ctx *ctx, const float *params, int64_t M, int32_t k, float *dist,
                     int32_t *idx);
 
+/* ---- training loop: optimiser step ------------------------------------------ */
+
+/* The paper optimises the Gaussians against the images (Sec. 3.2,
+ * "Optimizing 3D GS representations") without naming the optimiser or the
+ * parameter activations; these follow 3DGS practice.  Parameters are kept
+ * unconstrained ("raw"): raw = (p, log s, q, log rho); the model parameters
+ * the projection takes are params = (p, exp(log s), q, exp(log rho)) (the
+ * quaternion is normalised by the projection). */
+typedef struct gem_adam_config {
+  float lr[4];   /* learning rates: centre (A), log scale, quaternion, log density */
+  float beta1;   /* first-moment decay, in [0, 1)  (0.9)                           */
+  float beta2;   /* second-moment decay, in [0, 1) (0.999)                         */
+  float eps;     /* added to sqrt(v^), > 0          (1e-15 in 3DGS; 1e-8 typical)   */
+  int32_t step;  /* 1 on the first step: bias corrections 1 / (1 - beta^step)        */
+} gem_adam_config;
+
+/* One Adam step on raw [M][11] from grad = dL/dparams [M][11] (the output of
+ * gem_backward), chain rule through the activations included:
+ *   g_raw = grad (centre, quaternion),  grad * s (log s),  grad * rho (log rho)
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   raw -= lr_group * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ * then params = activation(raw).  Non-finite gradient entries count as 0.
+ *   raw, m, v, params  device float [M][11] (m, v start at 0), updated;
+ *   iso_scale          device float [M] or NULL: when given, the three scale
+ *                      entries of Gaussian j are set to iso_scale[j] (raw to
+ *                      its log) and not learnt: the isotropic-scaling ablation
+ *                      with s_j = the nearest-neighbour distance
+ *                      (gem_nn_distance), recomputed by the caller each step.
+ * Asynchronous.  Errors: GEM_EINVAL (M, pointers, hyper-parameters), GEM_ECUDA. */
+int gem_adam_step(gem_ctx *ctx, int64_t M, const gem_adam_config *cfg, float *raw, float *m,
+                  float *v, const float *grad, float *params, const float *iso_scale);
+
+/* params [M][11] = activation(raw [M][11]) (device arrays).  Asynchronous. */
+int gem_activate(gem_ctx *ctx, int64_t M, const float *raw, float *params);
+
 /* ---- allocation-free variant ---------------------------------------------- */
 
 /* Step a4 (gem_ctf_loss) for callers that cannot allocate device memory at

@@ -319,3 +319,46 @@ def fsc(X1, X2, apix: float, threshold: float = 0.143):
     den = np.sqrt(p1 * p2)
     curve = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
     return curve, (num, p1, p2), fsc_crossing(curve, d, apix, threshold)
+
+
+# ----------------------------------------------------------------------------
+# Training loop: parameter activations and the Adam step (Sec. 3.2
+# "Optimizing 3D GS representations"; the paper names neither, so these are
+# the 3DGS practice: scales and densities through exp, Adam).
+# ----------------------------------------------------------------------------
+
+LOG_ENTRIES = np.array([3, 4, 5, 10])
+GROUP_OF = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3])
+
+
+def activate(raw) -> np.ndarray:
+    """params = (p, exp(log s), q, exp(log rho)) from raw = (p, log s, q, log rho)."""
+    p = _f64(raw).copy()
+    p[:, LOG_ENTRIES] = np.exp(p[:, LOG_ENTRIES])
+    return p
+
+
+def adam_step(raw, m, v, grad, lr, step: int, beta1=0.9, beta2=0.999, eps=1e-8, iso_scale=None):
+    """One Adam step (Kingma and Ba, Algorithm 1) on raw parameters, the
+    gradient given with respect to activate(raw).  Returns (raw, m, v, params)."""
+    raw, m, v, grad = _f64(raw).copy(), _f64(m).copy(), _f64(v).copy(), _f64(grad)
+    m0, v0 = m.copy(), v.copy()
+    params = activate(raw)
+    g = grad.copy()
+    g[:, LOG_ENTRIES] *= params[:, LOG_ENTRIES]  # d/dlog x = x d/dx
+    g[~np.isfinite(g)] = 0.0
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    lrs = np.asarray(lr, dtype=np.float64)[GROUP_OF]
+    new = raw - lrs[None, :] * mhat / (np.sqrt(vhat) + eps)
+    params = activate(new)
+    if iso_scale is not None:
+        # isotropic ablation: the scales are the given distances, not learnt
+        s = _f64(iso_scale)
+        new[:, 3:6] = np.log(s)[:, None]
+        params[:, 3:6] = s[:, None]
+        m[:, 3:6] = m0[:, 3:6]
+        v[:, 3:6] = v0[:, 3:6]
+    return new, m, v, params

@@ -49,6 +49,16 @@ class gem_config(ctypes.Structure):
     ]
 
 
+class gem_adam_config(ctypes.Structure):
+    _fields_ = [
+        ("lr", ctypes.c_float * 4),
+        ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("step", ctypes.c_int32),
+    ]
+
+
 # name -> (restype, argtypes)
 _P, _I32, _I64, _F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
 SIGNATURES = {
@@ -76,6 +86,8 @@ SIGNATURES = {
     "gem_nn_distance": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P]),
     "gem_query": (ctypes.c_int, [_P, _P, _I64, _F, _P]),
     "gem_fsc": (ctypes.c_int, [_P, _P, _P, _F, _P, _P, _P]),
+    "gem_adam_step": (ctypes.c_int, [_P, _I64, ctypes.POINTER(gem_adam_config), _P, _P, _P, _P, _P, _P]),
+    "gem_activate": (ctypes.c_int, [_P, _I64, _P, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
@@ -282,6 +294,26 @@ class Context:
         self._rc(self.lib.gem_fsc(self.h, _ptr(map1), _ptr(map2), threshold, _ptr(fsc), _ptr(sums),
                                   _ptr(res)))
         return fsc, sums, res
+
+    def gem_adam_step(self, raw, m, v, grad, params, lr, step: int, beta1=0.9, beta2=0.999,
+                      eps=1e-8, iso_scale=None):
+        """One Adam step on the raw parameters (lr: 4 group learning rates)."""
+        M = raw.shape[0]
+        for name, x in (("raw", raw), ("m", m), ("v", v), ("grad", grad), ("params", params)):
+            _check(x, name, (M, NPAR))
+        _check(iso_scale, "iso_scale", (M,), optional=True)
+        cfg = gem_adam_config()
+        for k in range(4):
+            cfg.lr[k] = float(lr[k])
+        cfg.beta1, cfg.beta2, cfg.eps, cfg.step = beta1, beta2, eps, int(step)
+        self._rc(self.lib.gem_adam_step(self.h, M, ctypes.byref(cfg), _ptr(raw), _ptr(m), _ptr(v),
+                                        _ptr(grad), _ptr(params), _ptr(iso_scale)))
+
+    def gem_activate(self, raw, params):
+        M = raw.shape[0]
+        _check(raw, "raw", (M, NPAR))
+        _check(params, "params", (M, NPAR))
+        self._rc(self.lib.gem_activate(self.h, M, _ptr(raw), _ptr(params)))
 
     def gem_nn_distance(self, params, k: int, dist=None, idx=None):
         """-> (dist [M][k] float32, idx [M][k] int32) of the centres' k nearest neighbours."""

@@ -581,6 +581,44 @@ int gem_fsc(gem_ctx *c, const float *map1, const float *map2, float threshold, d
   return GEM_OK;
 }
 
+int gem_adam_step(gem_ctx *c, int64_t M, const gem_adam_config *cfg, float *raw, float *m,
+                  float *v, const float *grad, float *params, const float *iso_scale) {
+  if (!c) return GEM_EINVAL;
+  if (!cfg || !raw || !m || !v || !grad || !params)
+    return fail(c, GEM_EINVAL, "null argument");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) ||
+      !(cfg->eps > 0.f) || cfg->step < 1)
+    return fail(c, GEM_EINVAL, "need 0 <= beta < 1, eps > 0, step >= 1");
+  AdamArgs a;
+  for (int k = 0; k < 4; ++k) {
+    if (!(cfg->lr[k] >= 0.f) || !isfinite(cfg->lr[k]))
+      return fail(c, GEM_EINVAL, "learning rates must be finite and >= 0");
+    a.lr[k] = cfg->lr[k];
+  }
+  a.beta1 = cfg->beta1;
+  a.beta2 = cfg->beta2;
+  a.eps = cfg->eps;
+  a.c1 = (float)(1.0 / (1.0 - pow((double)cfg->beta1, (double)cfg->step)));
+  a.c2 = (float)(1.0 / (1.0 - pow((double)cfg->beta2, (double)cfg->step)));
+  cudaError_t e = launch_adam(a, M, raw, m, v, grad, params, iso_scale, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adam");
+  return GEM_OK;
+}
+
+int gem_activate(gem_ctx *c, int64_t M, const float *raw, float *params) {
+  if (!c) return GEM_EINVAL;
+  if (!raw || !params) return fail(c, GEM_EINVAL, "null argument");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  cudaError_t e = launch_activate(M, raw, params, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "activate");
+  return GEM_OK;
+}
+
 int gem_nn_distance(gem_ctx *c, const float *params, int64_t M, int32_t k, float *dist,
                     int32_t *idx) {
   if (!c) return GEM_EINVAL;

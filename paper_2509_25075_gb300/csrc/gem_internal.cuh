@@ -267,6 +267,16 @@ cudaError_t launch_query_prep(const float *params, int64_t M, int norm_mode, int
 cudaError_t launch_slice_prep(const QueryPrep *qp, int64_t M, int k0, int nslice, float apix,
                               int d, float l2tau, Rec *rec, cudaStream_t st);
 
+// gem_adam.cu
+struct AdamArgs {
+  float lr[4];  // centre, log scale, quaternion, log density
+  float beta1, beta2, eps;
+  float c1, c2;  // bias corrections 1 / (1 - beta^t)
+};
+cudaError_t launch_adam(const AdamArgs &a, int64_t M, float *raw, float *m, float *v,
+                        const float *grad, float *params, const float *iso, cudaStream_t st);
+cudaError_t launch_activate(int64_t M, const float *raw, float *params, cudaStream_t st);
+
 // gem_knn.cu
 struct KnnGrid {
   float lo[3];  // corner of the centres' bounding box
