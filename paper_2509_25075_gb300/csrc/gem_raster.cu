@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
     int64_t M, int d, float l2tau, float *__restrict__ proj,
     unsigned long long *__restrict__ kept) {
   __shared__ float4 sa[kWin], sb[kWin];
-  __shared__ unsigned char blist[16][kWin];          // per block: staged slots touching it
+  __shared__ unsigned char blist[16][kWin + 4];      // per block: staged slots touching it
+                                                      // (rows padded: lists in different banks)
   __shared__ unsigned short wcnt[kThreads / 32][16];  // per warp, per block: how many
   __shared__ unsigned wbal[kThreads / 32][16];        // per warp, per block: which lanes
   __shared__ float2 pix[kTile * kTile];               // per-pixel compensated sums over windows
