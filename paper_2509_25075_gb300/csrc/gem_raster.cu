@@ -7,13 +7,18 @@
 // (computed once by the binning).  A Gaussian therefore costs 16 pixel
 // evaluations per block it touches, instead of 256 per tile.
 //
-// a3: Eq. render restricted by Eq. accu.  The 16 blocks are owned by 8
-//     threads each (two horizontally adjacent pixels per thread).  Records
-//     are staged 128 at a time; ballots give every block the list of staged
-//     records that touch it, in list order, and the block's threads walk
-//     that list.  So each pixel adds its kept terms from the lowest depth to
-//     the highest, deterministically (float partials per 128 records, summed
-//     in double).
+// a3: Eq. render restricted by Eq. accu.  Records are staged 256 at a time;
+//     ballots give every 4x4 block the list of staged records that touch it,
+//     in list order.  A group of 8 threads takes one block (blocks by
+//     decreasing list length, so a warp's groups run loops of similar
+//     length); each thread takes two pixel rows of the block and every
+//     fourth record of the block's list, and evaluates its 8 pixels for the
+//     record from registers (the record is read from shared memory once per
+//     8 evaluations).  At the end of the window a fixed butterfly over the 4
+//     lanes sharing the rows sums the partials, each lane keeping two
+//     pixels, and the window's sums join the pixels' running sums with Kahan
+//     compensation.  Each pixel's sum is therefore
+//     formed window by window in depth order, deterministically.
 // a5: the "efficient gradient" of Sec. 1 (iii) / Sec. 3.2: only pairs kept by
 //     Eq. accu.  Each warp takes every fourth 64-record window of the list,
 //     sorts it by block count and runs it as two rounds of 32 records with
@@ -34,31 +39,35 @@ __device__ __forceinline__ float2 kahan_add(float2 s, float x) {
   const float t = s.x + y;
   return make_float2(t, (t - s.x) - y);
 }
-constexpr int kWin = 128;  // records staged per window
+constexpr int kSub = 2;                // forward: records staged per thread per window
+constexpr int kWin = kThreads * kSub;  // records staged per window
 
 // kCount = true: the same walk, counting kept pairs into kept[0] and
 // evaluated pairs into kept[1] instead of writing the projection
 // (inspection only, never on the timed path).
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
+__global__ void __launch_bounds__(kThreads, 12) raster_fwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, float *__restrict__ proj,
     unsigned long long *__restrict__ kept) {
+  constexpr int kWarps = kThreads / 32;
   __shared__ float4 sa[kWin], sb[kWin];
-  __shared__ unsigned char blist[16][kWin + 4];      // per block: staged slots touching it
-                                                      // (rows padded: lists in different banks)
-  __shared__ unsigned short wcnt[kThreads / 32][16];  // per warp, per block: how many
-  __shared__ unsigned wbal[kThreads / 32][16];        // per warp, per block: which lanes
-  __shared__ float2 pix[kTile * kTile];               // per-pixel compensated sums over windows
-  __shared__ unsigned char sorder[16], slen[16];      // blocks by list length
+  using Slot = unsigned char;
+  __shared__ Slot blist[16][kWin + 4];            // per block: staged slots touching it
+                                                   // (rows padded: lists in different banks)
+  __shared__ unsigned short wcnt[kSub][kWarps][16];  // per sub-window, warp, block: how many
+  __shared__ unsigned wbal[kSub][kWarps][16];        // per sub-window, warp, block: which lanes
+  __shared__ float2 pix[kTile * kTile];              // per-pixel compensated sums over windows
+  __shared__ unsigned char sorder[16];               // blocks by list length
+  __shared__ unsigned short slen[16];
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // thread group g (8 threads) takes, in each window, the block with the
-  // g-th longest list; within it, pair pp: row pp/2, columns 2 (pp%2) + {0,1}
+  // g-th longest list
   const int grp = threadIdx.x >> 3, pp = threadIdx.x & 7;
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
@@ -71,31 +80,43 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
   for (int64_t base = s; base < e; base += kWin) {
     const int n = (int)min((int64_t)kWin, e - base);
     __syncthreads();  // previous window fully consumed
-    unsigned m = 0;
-    if (threadIdx.x < n) {
-      const Rec r = rb[list[base + threadIdx.x]];
-      m = lmask[base + threadIdx.x];
-      sa[threadIdx.x] = r.a;
-      sb[threadIdx.x] = r.b;
-    }
-    unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
+    // record slot u * kThreads + threadIdx.x of sub-window u
+    unsigned m[kSub];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      unsigned bk = __ballot_sync(0xffffffffu, (m >> k) & 1u);
-      if (lane == k) mybal = bk;
-    }
-    if (lane < 16) {
-      wcnt[warp][lane] = (unsigned short)__popc(mybal);
-      wbal[warp][lane] = mybal;
+    for (int u = 0; u < kSub; ++u) {
+      const int slot = u * kThreads + threadIdx.x;
+      m[u] = 0;
+      if (slot < n) {
+        const Rec r = rb[list[base + slot]];
+        m[u] = lmask[base + slot];
+        sa[slot] = r.a;
+        sb[slot] = r.b;
+      }
+      unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const unsigned bk = __ballot_sync(0xffffffffu, (m[u] >> k) & 1u);
+        if (lane == k) mybal = bk;
+      }
+      if (lane < 16) {
+        wcnt[u][warp][lane] = (unsigned short)__popc(mybal);
+        wbal[u][warp][lane] = mybal;
+      }
     }
     __syncthreads();
-    // place my record in the lists of its blocks: after the records of lower
-    // warps and lower lanes touching the same block
-    for (unsigned mm = m; mm; mm &= mm - 1) {
-      const int k = __ffs(mm) - 1;
-      int pos = __popc(wbal[warp][k] & lt);
-      for (int w = 0; w < warp; ++w) pos += wcnt[w][k];
-      blist[k][pos] = (unsigned char)threadIdx.x;
+    // place my records in the lists of their blocks: after the records of
+    // earlier sub-windows, lower warps and lower lanes touching the same block
+#pragma unroll
+    for (int u = 0; u < kSub; ++u) {
+      for (unsigned mm = m[u]; mm; mm &= mm - 1) {
+        const int k = __ffs(mm) - 1;
+        int pos = __popc(wbal[u][warp][k] & lt);
+        for (int v = 0; v < u; ++v)
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) pos += wcnt[v][w][k];
+        for (int w = 0; w < warp; ++w) pos += wcnt[u][w][k];
+        blist[k][pos] = (Slot)(u * kThreads + threadIdx.x);
+      }
     }
     // warp 0 orders the blocks by list length (longest first, ties by
     // index): group g takes block sorder[g]
@@ -103,7 +124,9 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
       int len = 0;
       if (lane < 16)
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) len += wcnt[w][lane];
+        for (int u = 0; u < kSub; ++u)
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) len += wcnt[u][w][lane];
       int rank = 0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
@@ -112,39 +135,72 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(
       }
       if (lane < 16) {
         sorder[rank] = (unsigned char)lane;
-        slen[rank] = (unsigned char)len;
+        slen[rank] = (unsigned short)len;
       }
     }
     __syncthreads();
+    // group g takes block sorder[g]; thread pp of the group takes rows
+    // 2h, 2h + 1 of the block (h = pp / 4) for every fourth record of the
+    // block's list (records i = pp % 4 mod 4): eight pixels per record
     const int blk = sorder[grp], nb = slen[grp];
-    const int px_ = x0 + 4 * (blk & 3) + 2 * (pp & 1);
-    const int py_ = y0 + 4 * (blk >> 2) + (pp >> 1);
-    const float X0 = (float)px_, X1 = X0 + 1.f, Y = (float)py_;
-    float p0 = 0.f, p1 = 0.f;
-    for (int i = 0; i < nb; ++i) {
+    const int h = pp >> 2, ph = pp & 3;
+    const float X0 = (float)(x0 + 4 * (blk & 3)), Y0 = (float)(y0 + 4 * (blk >> 2) + 2 * h);
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    for (int i = ph; i < nb; i += 4) {
       const int slot = blist[blk][i];
       const float4 A = sa[slot];
       const float4 Bv = sb[slot];
-      const float dy = Y - A.y;
-      const float bdy = A.w * dy;
-      const float cdy = fmaf(Bv.x * dy, dy, Bv.y);
-      const float dx0 = X0 - A.x, dx1 = X1 - A.x;
-      const float e0 = fmaf(fmaf(A.z, dx0, bdy), dx0, cdy);
-      const float e1 = fmaf(fmaf(A.z, dx1, bdy), dx1, cdy);
-      if (kCount) {
-        nkept += (e0 > l2tau) + (e1 > l2tau);
-        neval += 2;
-      } else {
-        const float v0 = ex2_approx(e0), v1 = ex2_approx(e1);
-        p0 += e0 > l2tau ? v0 : 0.f;
-        p1 += e1 > l2tau ? v1 : 0.f;
+      float dx[4], cadx[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        dx[c] = X0 + (float)c - A.x;
+        cadx[c] = A.z * dx[c];
       }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
+        const float dy = Y0 + (float)r - A.y;
+        const float bdy = A.w * dy;
+        const float cdy = fmaf(Bv.x * dy, dy, Bv.y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float ev = fmaf(cadx[c] + bdy, dx[c], cdy);
+          if (kCount) {
+            nkept += ev > l2tau;
+          } else {
+            const float v = ex2_approx(ev);
+            if (ev > l2tau) acc[4 * r + c] += v;
+          }
+        }
+      }
+      if (kCount) neval += 8;
     }
-    // the window's sum joins the pixel's running sum (one owner per pixel
+    // reduce-scatter over the 4 lanes sharing the rows (lane bit 1 picks the
+    // row, bit 0 the column pair): lane pp ends with row 2h + bit 1, columns
+    // 2 bit 0 + {0, 1}
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool hi = (pp & 2) != 0;
+      const float send = hi ? acc[q] : acc[4 + q];
+      const float keep = hi ? acc[4 + q] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool hi = (pp & 1) != 0;
+      const float send = hi ? acc[q] : acc[2 + q];
+      const float keep = hi ? acc[2 + q] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+    // the window's sums join the pixels' running sums (one owner per pixel
     // per window, windows in list order; Kahan-compensated)
-    const int pl = (py_ - y0) * kTile + (px_ - x0);
-    pix[pl] = kahan_add(pix[pl], p0);
-    pix[pl + 1] = kahan_add(pix[pl + 1], p1);
+    const int pl = (4 * (blk >> 2) + 2 * h + ((pp >> 1) & 1)) * kTile + 4 * (blk & 3) + 2 * (pp & 1);
+    if (!kCount) {
+      pix[pl] = kahan_add(pix[pl], acc[0]);
+      pix[pl + 1] = kahan_add(pix[pl + 1], acc[1]);
+    }
   }
   if (kCount) {
     for (int o = 16; o > 0; o >>= 1) {
