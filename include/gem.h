@@ -263,6 +263,29 @@ int gem_fsc(gem_ctx *ctx, const float *map1, const float *map2, float threshold,
 int gem_nn_distance(gem_ctx *ctx, const float *params, int64_t M, int32_t k, float *dist,
                     int32_t *idx);
 
+/* ---- FP64 check mode --------------------------------------------------------- */
+
+/* Steps a1-a6 in double precision by the plain dense forms: every pixel
+ * against every Gaussian with exp() in double, explicit separable DFTs for
+ * the CTF, the same moments and chain rule as the float path.  For checking
+ * the method's arithmetic (agreement with an FP64 reference to ~1e-12), not
+ * for speed: the cost is B d^2 M exponentials per projection and again per
+ * backward, and O(d^3) per image for the CTF.  The context's d, apix, tau,
+ * norm_mode and ablation flags apply; all arrays are double, on the device,
+ * caller-owned, with the layouts of the float calls; as for gem_project,
+ * params, R and t of gem_project_f64 are read again by
+ * gem_project_backward_f64 and must stay valid and unchanged until then.
+ * The first call
+ * allocates about (80 max_B max_M + 48 max_B d^2) bytes of scratch that the
+ * context keeps.  Asynchronous.  Errors: GEM_EINVAL, GEM_ENOMEM, GEM_ECUDA,
+ * GEM_ESTATE (backward without a projection). */
+int gem_project_f64(gem_ctx *ctx, const double *params, int64_t M, int32_t B, const double *R,
+                    const double *t, double *proj);
+int gem_ctf_loss_f64(gem_ctx *ctx, int32_t B, const double *proj, const double *ctf,
+                     const double *ctf_params, const double *images, double *pred,
+                     double *dproj, double *loss_img, double *loss);
+int gem_project_backward_f64(gem_ctx *ctx, const double *dproj, double *grad);
+
 /* ---- training loop: optimiser step ------------------------------------------ */
 
 /* The paper optimises the Gaussians against the images (Sec. 3.2,

@@ -88,6 +88,9 @@ SIGNATURES = {
     "gem_fsc": (ctypes.c_int, [_P, _P, _P, _F, _P, _P, _P]),
     "gem_adam_step": (ctypes.c_int, [_P, _I64, ctypes.POINTER(gem_adam_config), _P, _P, _P, _P, _P, _P]),
     "gem_activate": (ctypes.c_int, [_P, _I64, _P, _P]),
+    "gem_project_f64": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "gem_ctf_loss_f64": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gem_project_backward_f64": (ctypes.c_int, [_P, _P, _P]),
 }
 
 STAGES = ["prep", "bin", "raster_fwd", "ctf", "raster_bwd", "prep_bwd"]
@@ -165,6 +168,8 @@ class Context:
         self.h = h
         self.M = None
         self.B = None
+        self.M64 = None
+        self.B64 = None
 
     # -- plumbing ------------------------------------------------------------
     def _rc(self, rc):
@@ -294,6 +299,38 @@ class Context:
         self._rc(self.lib.gem_fsc(self.h, _ptr(map1), _ptr(map2), threshold, _ptr(fsc), _ptr(sums),
                                   _ptr(res)))
         return fsc, sums, res
+
+    # -- FP64 check mode ---------------------------------------------------------
+    def gem_project_f64(self, params, R, t, proj):
+        M, B, d = params.shape[0], R.shape[0], self.d
+        f8 = torch.float64
+        _check(params, "params", (M, NPAR), f8)
+        _check(R, "R", (B, 3, 3), f8)
+        _check(t, "t", (B, 2), f8)
+        _check(proj, "proj", (B, d, d), f8)
+        self._rc(self.lib.gem_project_f64(self.h, _ptr(params), M, B, _ptr(R), _ptr(t), _ptr(proj)))
+        self.M64, self.B64 = M, B
+
+    def gem_ctf_loss_f64(self, proj, images, ctf=None, ctf_params=None, pred=None, dproj=None,
+                         loss_img=None, loss=None):
+        B, d, f8 = proj.shape[0], self.d, torch.float64
+        _check(proj, "proj", (B, d, d), f8)
+        _check(images, "images", (B, d, d), f8)
+        _check(ctf, "ctf", (B, d, d // 2 + 1), f8, optional=True)
+        _check(ctf_params, "ctf_params", (B, 8), f8, optional=True)
+        for name, x in (("pred", pred), ("dproj", dproj)):
+            _check(x, name, (B, d, d), f8, optional=True)
+        _check(loss_img, "loss_img", (B,), f8, optional=True)
+        _check(loss, "loss", (1,), f8, optional=True)
+        self._rc(self.lib.gem_ctf_loss_f64(self.h, B, _ptr(proj), _ptr(ctf), _ptr(ctf_params),
+                                           _ptr(images), _ptr(pred), _ptr(dproj), _ptr(loss_img),
+                                           _ptr(loss)))
+
+    def gem_project_backward_f64(self, dproj, grad):
+        f8 = torch.float64
+        _check(dproj, "dproj", (self.B64, self.d, self.d), f8)
+        _check(grad, "grad", (self.M64, NPAR), f8)
+        self._rc(self.lib.gem_project_backward_f64(self.h, _ptr(dproj), _ptr(grad)))
 
     def gem_adam_step(self, raw, m, v, grad, params, lr, step: int, beta1=0.9, beta2=0.999,
                       eps=1e-8, iso_scale=None):

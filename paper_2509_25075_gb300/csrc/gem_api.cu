@@ -44,6 +44,18 @@ struct gem_ctx {
   // FSC scratch, allocated by the first gem_fsc: two d^3 complex volumes
   float2 *fscP = nullptr, *fscQ = nullptr;
   double *fsc_part = nullptr;
+  // FP64 check mode scratch, allocated by the first *_f64 call
+  struct {
+    G64 *gp = nullptr;
+    V64 *rec = nullptr;
+    double *mom = nullptr;
+    double2 *tw = nullptr, *Za = nullptr, *Zb = nullptr;
+    double *Hs = nullptr, *r = nullptr, *li = nullptr;
+    bool have = false;  // a projection to differentiate
+    const double *params = nullptr, *R = nullptr, *t = nullptr;
+    int64_t M = 0;
+    int B = 0;
+  } f64;
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -578,6 +590,77 @@ int gem_fsc(gem_ctx *c, const float *map1, const float *map2, float threshold, d
   cudaError_t e = launch_fsc(d, c->cfg.apix, threshold, c->plan, c->tw, map1, map2, c->fscP,
                              c->fscQ, c->fsc_part, fsc, sums, resolution, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fsc");
+  return GEM_OK;
+}
+
+static int f64_scratch(gem_ctx *c) {
+  if (c->f64.gp) return GEM_OK;
+  const gem_config &g = c->cfg;
+  const size_t BM = (size_t)g.max_B * g.max_M, n = (size_t)g.max_B * g.d * g.d;
+  if (!alloc(c, &c->f64.gp, g.max_M) || !alloc(c, &c->f64.rec, BM) ||
+      !alloc(c, &c->f64.mom, BM * 6) || !alloc(c, &c->f64.tw, (size_t)g.d) ||
+      !alloc(c, &c->f64.Za, n) || !alloc(c, &c->f64.Zb, n) || !alloc(c, &c->f64.Hs, n) ||
+      !alloc(c, &c->f64.r, n) || !alloc(c, &c->f64.li, (size_t)g.max_B)) {
+    c->f64.gp = nullptr;
+    return fail(c, GEM_ENOMEM, "FP64 check-mode scratch allocation failed");
+  }
+  return GEM_OK;
+}
+
+int gem_project_f64(gem_ctx *c, const double *params, int64_t M, int32_t B, const double *R,
+                    const double *t, double *proj) {
+  if (!c) return GEM_EINVAL;
+  if (!params || !R || !t || !proj) return fail(c, GEM_EINVAL, "null pointer argument");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  if (B < 1 || B > c->cfg.max_B)
+    return fail(c, GEM_EINVAL, "B=%d outside 1..max_B=%d", B, c->cfg.max_B);
+  int rc = f64_scratch(c);
+  if (rc) return rc;
+  const gem_config &g = c->cfg;
+  c->f64.have = false;
+  cudaError_t e = launch_f64_project(params, M, B, R, t, (double)g.apix, g.d, g.norm_mode,
+                                     shape_flags(g), (double)g.tau, c->f64.gp, c->f64.rec, proj,
+                                     c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "project f64");
+  c->f64.have = true;
+  c->f64.params = params;
+  c->f64.R = R;
+  c->f64.t = t;
+  c->f64.M = M;
+  c->f64.B = B;
+  return GEM_OK;
+}
+
+int gem_ctf_loss_f64(gem_ctx *c, int32_t B, const double *proj, const double *ctf,
+                     const double *ctf_params, const double *images, double *pred,
+                     double *dproj, double *loss_img, double *loss) {
+  if (!c) return GEM_EINVAL;
+  if (!proj || !images) return fail(c, GEM_EINVAL, "null proj or images");
+  if ((ctf == nullptr) == (ctf_params == nullptr))
+    return fail(c, GEM_EINVAL, "pass exactly one of ctf and ctf_params");
+  if (B < 1 || B > c->cfg.max_B)
+    return fail(c, GEM_EINVAL, "B=%d outside 1..max_B=%d", B, c->cfg.max_B);
+  int rc = f64_scratch(c);
+  if (rc) return rc;
+  cudaError_t e = launch_f64_ctf_loss(c->cfg.d, B, (double)c->cfg.apix, proj, ctf, ctf_params,
+                                      images, pred, dproj, loss_img, loss, c->f64.tw, c->f64.Hs,
+                                      c->f64.Za, c->f64.Zb, c->f64.r, c->f64.li, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ctf_loss f64");
+  return GEM_OK;
+}
+
+int gem_project_backward_f64(gem_ctx *c, const double *dproj, double *grad) {
+  if (!c) return GEM_EINVAL;
+  if (!dproj || !grad) return fail(c, GEM_EINVAL, "null dproj or grad");
+  if (!c->f64.have) return fail(c, GEM_ESTATE, "no FP64 projection to differentiate");
+  const gem_config &g = c->cfg;
+  cudaError_t e = launch_f64_backward(c->f64.params, c->f64.gp, c->f64.rec, c->f64.M, c->f64.B,
+                                      c->f64.R, c->f64.t, (double)g.apix, g.d, g.norm_mode,
+                                      shape_flags(g), (double)g.tau, dproj, c->f64.mom, grad,
+                                      c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward f64");
   return GEM_OK;
 }
 

@@ -267,6 +267,27 @@ cudaError_t launch_query_prep(const float *params, int64_t M, int norm_mode, int
 cudaError_t launch_slice_prep(const QueryPrep *qp, int64_t M, int k0, int nslice, float apix,
                               int d, float l2tau, Rec *rec, cudaStream_t st);
 
+// gem_f64.cu (FP64 check mode)
+struct G64 {
+  double p[3], sig[6], lnk;
+  bool valid;
+};
+struct V64 {
+  double px, py, cxx, cxy, cyy, lnA;  // lnA = -inf: contributes nothing
+};
+cudaError_t launch_f64_project(const double *params, int64_t M, int B, const double *R,
+                               const double *t, double apix, int d, int norm_mode, int shape,
+                               double tau, G64 *gp, V64 *rec, double *proj, cudaStream_t st);
+cudaError_t launch_f64_backward(const double *params, const G64 *gp, const V64 *rec, int64_t M,
+                                int B, const double *R, const double *t, double apix, int d,
+                                int norm_mode, int shape, double tau, const double *dproj,
+                                double *mom, double *grad, cudaStream_t st);
+cudaError_t launch_f64_ctf_loss(int d, int B, double apix, const double *proj, const double *ctf,
+                                const double *prm, const double *images, double *pred,
+                                double *dproj, double *loss_img, double *loss, double2 *tw,
+                                double *Hs, double2 *Za, double2 *Zb, double *r, double *li,
+                                cudaStream_t st);
+
 // gem_adam.cu
 struct AdamArgs {
   float lr[4];  // centre, log scale, quaternion, log density
