@@ -45,10 +45,10 @@ EX2_PER_CLK_PER_SM = 32
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "238b5de6104e3e2c",
+    "source_sha256_16": "7f78e3c1e30d1c81",
     "workload": "A2",
-    "raster_fwd": 295.571456e6 + 18.490624e6,
-    "raster_bwd": 386.912768e6 + 93.806592e6,
+    "raster_fwd": 296.805376e6 + 18.556160e6,
+    "raster_bwd": 387.495424e6 + 93.927936e6,
 }
 
 
