@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *__restrict__ 
   for (int c = 0; c < nch; ++c) col[(int64_t)c * 256] += base;
 }
 
-// Lanes of the warp holding the same 9-bit value: one ballot per bit.
+// Lanes of the warp holding the same 9-bit value: one ballot per bit
+// (faster here than a match instruction).
 __device__ __forceinline__ unsigned same_value_lanes(int v) {
   unsigned p = 0xffffffffu;
 #pragma unroll
@@ -185,6 +186,7 @@ struct ChunkStage {
   Ell ell[kChunkT];
   uint32_t j[kChunkT];
   int rect[kChunkT];      // tx0 | ty0 << 8 | width << 16 (0 width: no tile)
+  float inv_w[kChunkT];   // 1 / width, to split a candidate index into rows
   int off[kChunkT + 1];   // exclusive prefix of candidate counts; off[kChunkT] = total
   int wsum[kChunkT / 32];
   unsigned char owner[kOwnerCap];  // owner slot of each candidate (when they fit)
@@ -206,6 +208,7 @@ __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict
       const int w = tr.tx1 - tr.tx0 + 1;
       ncand = w * (tr.ty1 - tr.ty0 + 1);
       packed = tr.tx0 | (tr.ty0 << 8) | (w << 16);
+      S.inv_w[i] = 1.f / (float)w;
     }
   }
   S.rect[i] = packed;
@@ -229,6 +232,18 @@ __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict
   if (total <= kOwnerCap)
     for (int q = 0; q < ncand; ++q) S.owner[my + q] = (unsigned char)i;
   __syncthreads();
+}
+
+// Tile of candidate q (row-major in its rectangle) of a staged Gaussian.
+// q < 48 * 48 and w <= 48, so (q + 1/2) / w in float32 is at least 1 / (2 w)
+// away from an integer and its floor is the exact row.
+__device__ __forceinline__ void candidate_tile(const ChunkStage &S, int o, int q, int &tx,
+                                               int &ty) {
+  const int pr = S.rect[o];
+  const int w = (pr >> 16) & 0xffff;
+  const int row = (int)(((float)q + 0.5f) * S.inv_w[o]);
+  tx = (pr & 0xff) + (q - row * w);
+  ty = ((pr >> 8) & 0xff) + row;
 }
 
 // Owner (Gaussian slot) of candidate k: from the byte map when the chunk's
@@ -260,9 +275,8 @@ __global__ void __launch_bounds__(kChunkT) tile_count_kernel(const Rec *__restri
   const int total = S.off[kChunkT];
   for (int k = threadIdx.x; k < total; k += blockDim.x) {
     const int o = candidate_owner(S, k, total);
-    const int q = k - S.off[o], pr = S.rect[o];
-    const int w = (pr >> 16) & 0xffff;
-    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    int tx, ty;
+    candidate_tile(S, o, k - S.off[o], tx, ty);
     if (tile_hit(S.ell[o], tx * kTile, ty * kTile)) atomicAdd(&tc[ty * nt + tx], 1u);
   }
   __syncthreads();
@@ -355,9 +369,8 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   const int total = S.off[kChunkT];
   for (int k = threadIdx.x; k < total; k += blockDim.x) {
     const int o = candidate_owner(S, k, total);
-    const int q = k - S.off[o], pr = S.rect[o];
-    const int w = (pr >> 16) & 0xffff;
-    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    int tx, ty;
+    candidate_tile(S, o, k - S.off[o], tx, ty);
     if (tile_hit(S.ell[o], tx * kTile, ty * kTile))
       atomicOr(&bm[(ty * nt + tx) * 8 + (o >> 5)], 1u << (o & 31));
   }
@@ -365,9 +378,8 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   const uint32_t *coff = tcnt + (int64_t)b * T * nch + c;
   for (int k = threadIdx.x; k < total; k += blockDim.x) {
     const int o = candidate_owner(S, k, total);
-    const int q = k - S.off[o], pr = S.rect[o];
-    const int w = (pr >> 16) & 0xffff;
-    const int tx = (pr & 0xff) + q % w, ty = ((pr >> 8) & 0xff) + q / w;
+    int tx, ty;
+    candidate_tile(S, o, k - S.off[o], tx, ty);
     const int t = ty * nt + tx;
     const uint32_t *bw = bm + t * 8;
     const int word = o >> 5;
@@ -388,14 +400,16 @@ static int tile_smem_bytes(int d) {
   return nt * nt * 8 * (int)sizeof(uint32_t);
 }
 
+// The dynamic shared memory of both tile kernels (bitmaps, counters) is
+// declared for every image side, so that it never depends on what the
+// static part leaves of the default 48 KB.
 cudaError_t bin_configure(int d) {
-  int smem = tile_smem_bytes(d);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(tile_scatter_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const int smem = tile_smem_bytes(d);
+  cudaError_t e = cudaFuncSetAttribute(tile_scatter_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (d / kTile) * (d / kTile) * (int)sizeof(uint32_t));
 }
 
 cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, int d,
