@@ -37,18 +37,31 @@ UNIT = "images/s"
 # SFU (MUFU) base-2 exponentials per clock per SM on sm_103a: 32, measured on
 # GB300 by a throughput probe (8 independent ex2.approx chains per thread, one
 # 1024-thread block per SM, clock64 span: 31.99 per clock per SM).  One
-# exponential is the irreducible cost of a kept (pixel, Gaussian) pair in
+# exponential is the irreducible SFU cost of a kept (pixel, Gaussian) pair in
 # both rasterisers.
 EX2_PER_CLK_PER_SM = 32
+# FP32 lanes of the FMA pipe per SM per clock (nominal 128; the same probe
+# with FFMA chains measured 123.6).  Packed float pairs save issue slots, not
+# FMA-pipe cycles.
+FP32_PER_CLK_PER_SM = 128
+# FP32 operations on the FMA pipe that the definition of a kept pair needs,
+# evaluated directly (the compare runs on the ALU pipe, the exponential on
+# the SFU):
+#   forward (Eq. render, Eq. accu): dx, dy (2); the exponent
+#     (ca dx + cb dy) dx + cc dy dy + log2 A (5); the accumulation (1)  -> 8
+#   backward (moments of g * value): dx, dy, exponent (7); w = g * value (1);
+#     the six moments w {1, dx, dy, dx^2, dx dy, dy^2}: 3 products, 5 adds or
+#     fused adds (8)                                                     -> 16
+FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 
 # DRAM bytes (read + write) per launch of each rasteriser at workload A2,
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "7f78e3c1e30d1c81",
+    "source_sha256_16": "293f148a62e6e98e",
     "workload": "A2",
-    "raster_fwd": 296.805376e6 + 18.556160e6,
-    "raster_bwd": 387.495424e6 + 93.927936e6,
+    "raster_fwd": 262.171904e6 + 17.494016e6,
+    "raster_bwd": 497.048576e6 + 141.650944e6,
 }
 
 
@@ -374,15 +387,20 @@ def main():
     per_stage = {k: v / args.steps for k, v in stage_ms.items()}
     dom = max(("raster_fwd", "raster_bwd"), key=lambda k: per_stage[k])
     mhz = clk.get("sm_mhz") or 1455.0
-    peak = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9  # Gpair/s
+    ops = FP32_OPS_PER_KEPT_PAIR[dom]
+    per_clk = min(FP32_PER_CLK_PER_SM / ops, EX2_PER_CLK_PER_SM)  # kept pairs per clock per SM
+    peak = sms * per_clk * mhz * 1e6 / 1e9  # Gpair/s
+    peak_sfu = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9
     achieved = kept / (per_stage[dom] / 1e3) / 1e9
     traffic = None
     if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] and w.name == CAPTURED_TRAFFIC["workload"]:
         traffic = CAPTURED_TRAFFIC[dom]
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-            "peak_note": f"{sms} SMs x {EX2_PER_CLK_PER_SM} ex2/clk/SM x {mhz:.0f} MHz median SM clock "
-                         f"under load (one SFU exponential per kept pair)",
+            "peak_note": f"{sms} SMs x min({FP32_PER_CLK_PER_SM} FP32 lanes / {ops} FMA-pipe ops per kept "
+                         f"pair, {EX2_PER_CLK_PER_SM} ex2) per clock x {mhz:.0f} MHz median SM clock under load",
+            "sfu_only": {"peak": peak_sfu, "frac": achieved / peak_sfu,
+                         "note": "one SFU exponential per kept pair, no other work counted"},
             "kept_pairs_per_launch": kept, "evaluated_pairs_per_launch": evaluated,
             "listed_pairs_per_launch": pairs}
 
@@ -461,9 +479,11 @@ def main():
         if nbatch == 1:
             qk, qv = ctx.gem_pair_stats()
             qa = qk / (q_ms / 1e3) / 1e9
+            qpeak = sms * min(FP32_PER_CLK_PER_SM / FP32_OPS_PER_KEPT_PAIR["raster_fwd"],
+                              EX2_PER_CLK_PER_SM) * mhz * 1e6 / 1e9
             query.update({"kept_pairs": qk, "evaluated_pairs": qv,
-                          "roofline": {"bound": "alu", "kernel": "whole query", "achieved": qa, "peak": peak,
-                                       "unit": "Gpair/s", "frac": qa / peak}})
+                          "roofline": {"bound": "alu", "kernel": "whole query", "achieved": qa, "peak": qpeak,
+                                       "unit": "Gpair/s", "frac": qa / qpeak}})
 
     cpu = None
     if rank == 0 and not args.no_cpu:

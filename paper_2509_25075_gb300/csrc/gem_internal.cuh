@@ -50,6 +50,20 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// 1.0f when a > b, else 0.0f (false for NaN operands).
+__device__ __forceinline__ float set_gt(float a, float b) {
+  float y;
+  asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+
+// Packed float32 pairs (sm_100 family): each component rounds exactly like
+// the scalar operation, two components per issued instruction.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // Rotation matrix of a unit quaternion (w, x, y, z), entry formula.
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
   R[0] = 1.f - 2.f * (y * y + z * z);

@@ -7,26 +7,26 @@
 // (computed once by the binning).  A Gaussian therefore costs 16 pixel
 // evaluations per block it touches, instead of 256 per tile.
 //
-// a3: Eq. render restricted by Eq. accu.  Records are staged 256 at a time;
-//     ballots give every 4x4 block the list of staged records that touch it,
-//     in list order.  A group of 8 threads takes one block (blocks by
-//     decreasing list length, so a warp's groups run loops of similar
-//     length); each thread takes two pixel rows of the block and every
-//     fourth record of the block's list, and evaluates its 8 pixels for the
-//     record from registers (the record is read from shared memory once per
-//     8 evaluations).  At the end of the window a fixed butterfly over the 4
-//     lanes sharing the rows sums the partials, each lane keeping two
-//     pixels, and the window's sums join the pixels' running sums with Kahan
-//     compensation.  Each pixel's sum is therefore
-//     formed window by window in depth order, deterministically.
+// a3: Eq. render restricted by Eq. accu.  Records are staged 256 at a time
+//     (a window); ballots lay the window's (block, record) items out block
+//     after block, each block's records in list order.  The items are cut
+//     into 128 equal runs, one per thread, so every thread does the same
+//     amount of work whatever the blocks' list lengths.  A thread evaluates
+//     the 16 pixels of the current block for each record of its run
+//     (packed float pairs), and writes the partial sums of every block it
+//     leaves (a piece) to shared memory; at the end of the window each pixel
+//     sums the pieces of its block in thread order and joins its running sum
+//     with Kahan compensation.  The result is deterministic and follows the
+//     list's depth order run by run.
 // a5: the "efficient gradient" of Sec. 1 (iii) / Sec. 3.2: only pairs kept by
-//     Eq. accu.  Each warp takes every fourth 64-record window of the list,
-//     sorts it by block count and runs it as two rounds of 32 records with
-//     neighbouring counts, one lane per record: the lane walks the record's
-//     blocks and accumulates six moments of g * value in registers.  No
-//     barrier couples the warps.  a6 turns the moments into parameter
-//     gradients.  One set of vector atomics per (tile, Gaussian) goes to
-//     global memory.
+//     Eq. accu.  Each warp takes 128-record windows of the list (the next one
+//     not yet taken), sorts the window by block count and runs it in rounds
+//     of 16 records with neighbouring counts, two lanes per record (two
+//     pixel rows of each block each): the lanes walk the record's blocks and
+//     accumulate six moments of g * value in registers (packed float
+//     pairs), then add their halves.  No barrier couples the warps.  a6 turns
+//     the moments into parameter gradients.  One set of vector atomics per
+//     (tile, Gaussian) goes to global memory.
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -41,50 +41,53 @@ __device__ __forceinline__ float2 kahan_add(float2 s, float x) {
 }
 constexpr int kSub = 2;                // forward: records staged per thread per window
 constexpr int kWin = kThreads * kSub;  // records staged per window
+static_assert(kThreads == 128, "the forward splits items with shifts by 7");
+constexpr int kFwdMinBlocks = 9;      // forward: CTAs per SM (its shared memory allows 9)
+constexpr int kBwdLanes = 2;          // backward: lanes sharing one record
+constexpr int kBwdPer = 4;            // backward: records per lane per warp window
 
 // kCount = true: the same walk, counting kept pairs into kept[0] and
 // evaluated pairs into kept[1] instead of writing the projection
 // (inspection only, never on the timed path).
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 12) raster_fwd_kernel(
+__global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, float *__restrict__ proj,
     unsigned long long *__restrict__ kept) {
   constexpr int kWarps = kThreads / 32;
+  constexpr int kPieces = 16 + kThreads - 1;
   __shared__ float4 sa[kWin], sb[kWin];
-  using Slot = unsigned char;
-  __shared__ Slot blist[16][kWin + 4];            // per block: staged slots touching it
-                                                   // (rows padded: lists in different banks)
+  __shared__ unsigned char flat[16 * kWin];           // staged slot of each (block, record) item,
+                                                      // blocks in order, records in list order
   __shared__ unsigned short wcnt[kSub][kWarps][16];  // per sub-window, warp, block: how many
   __shared__ unsigned wbal[kSub][kWarps][16];        // per sub-window, warp, block: which lanes
-  __shared__ float2 pix[kTile * kTile];              // per-pixel compensated sums over windows
-  __shared__ unsigned char sorder[16];               // blocks by list length
-  __shared__ unsigned short slen[16];
+  __shared__ int woff[kWarps][kSub][16];             // where a warp's records go in flat
+  __shared__ int pstart[kWarps][17];                 // block k's items: [pstart[k], pstart[k+1])
+  __shared__ float4 part[kPieces][4];                // piece (block k, thread u) at k + u
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // thread group g (8 threads) takes, in each window, the block with the
-  // g-th longest list
-  const int grp = threadIdx.x >> 3, pp = threadIdx.x & 7;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
   s = min(s, e);
   const Rec *rb = rec + (int64_t)b * M;
   const unsigned lt = (1u << lane) - 1u;
-  for (int i = threadIdx.x; i < kTile * kTile; i += kThreads) pix[i] = make_float2(0.f, 0.f);
+  // pixels owned across windows: two columns of one row of block ob
+  const int ob = tid >> 3, ow = tid & 7;
+  float2 own0 = make_float2(0.f, 0.f), own1 = make_float2(0.f, 0.f);  // Kahan (sum, comp)
   unsigned nkept = 0, neval = 0;
   for (int64_t base = s; base < e; base += kWin) {
     const int n = (int)min((int64_t)kWin, e - base);
     __syncthreads();  // previous window fully consumed
-    // record slot u * kThreads + threadIdx.x of sub-window u
+    // record slot u * kThreads + tid of sub-window u
     unsigned m[kSub];
 #pragma unroll
     for (int u = 0; u < kSub; ++u) {
-      const int slot = u * kThreads + threadIdx.x;
+      const int slot = u * kThreads + tid;
       m[u] = 0;
       if (slot < n) {
         const Rec r = rb[list[base + slot]];
@@ -104,102 +107,126 @@ __global__ void __launch_bounds__(kThreads, 12) raster_fwd_kernel(
       }
     }
     __syncthreads();
-    // place my records in the lists of their blocks: after the records of
-    // earlier sub-windows, lower warps and lower lanes touching the same block
+    // every warp: block lengths, their prefix (the items of all blocks laid
+    // out block after block) and where its own records go: after the
+    // records of earlier sub-windows and lower warps touching the block
+    {
+      int len = 0, wo[kSub];
+#pragma unroll
+      for (int u = 0; u < kSub; ++u) {
+        wo[u] = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+          if (w == warp) wo[u] = len;
+          if (lane < 16) len += wcnt[u][w][lane];
+        }
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane < 16) {
+        pstart[warp][lane] = incl - len;
+#pragma unroll
+        for (int u = 0; u < kSub; ++u) woff[warp][u][lane] = incl - len + wo[u];
+      }
+      if (lane == 15) pstart[warp][16] = incl;
+      __syncwarp();
+    }
 #pragma unroll
     for (int u = 0; u < kSub; ++u) {
       for (unsigned mm = m[u]; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
-        int pos = __popc(wbal[u][warp][k] & lt);
-        for (int v = 0; v < u; ++v)
-#pragma unroll
-          for (int w = 0; w < kWarps; ++w) pos += wcnt[v][w][k];
-        for (int w = 0; w < warp; ++w) pos += wcnt[u][w][k];
-        blist[k][pos] = (Slot)(u * kThreads + threadIdx.x);
-      }
-    }
-    // warp 0 orders the blocks by list length (longest first, ties by
-    // index): group g takes block sorder[g]
-    if (warp == 0) {
-      int len = 0;
-      if (lane < 16)
-#pragma unroll
-        for (int u = 0; u < kSub; ++u)
-#pragma unroll
-          for (int w = 0; w < kWarps; ++w) len += wcnt[u][w][lane];
-      int rank = 0;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int lq = __shfl_sync(0xffffffffu, len, q);
-        rank += (lq > len) || (lq == len && q < lane);
-      }
-      if (lane < 16) {
-        sorder[rank] = (unsigned char)lane;
-        slen[rank] = (unsigned short)len;
+        flat[woff[warp][u][k] + __popc(wbal[u][warp][k] & lt)] = (unsigned char)(u * kThreads + tid);
       }
     }
     __syncthreads();
-    // group g takes block sorder[g]; thread pp of the group takes rows
-    // 2h, 2h + 1 of the block (h = pp / 4) for every fourth record of the
-    // block's list (records i = pp % 4 mod 4): eight pixels per record
-    const int blk = sorder[grp], nb = slen[grp];
-    const int h = pp >> 2, ph = pp & 3;
-    const float X0 = (float)(x0 + 4 * (blk & 3)), Y0 = (float)(y0 + 4 * (blk >> 2) + 2 * h);
-    float acc[8];
+    // thread tid takes items [lo, hi) of the concatenation: a run of
+    // records of one block or a few consecutive blocks, 16 pixels each;
+    // each block it leaves (a piece) goes to part[k + tid]
+    const int *ps = pstart[0];
+    const int N = ps[16];
+    const int lo = (tid * N) >> 7, hi = ((tid + 1) * N) >> 7;
+    if (lo < hi) {
+      int k = 0;
+      while (ps[k + 1] <= lo) ++k;
+      float2 acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-    for (int i = ph; i < nb; i += 4) {
-      const int slot = blist[blk][i];
-      const float4 A = sa[slot];
-      const float4 Bv = sb[slot];
-      float dx[4], cadx[4];
+      for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+      float X0 = (float)(x0 + 4 * (k & 3)), Y0 = (float)(y0 + 4 * (k >> 2));
+      for (int i = lo; i < hi; ++i) {
+        if (i >= ps[k + 1]) {  // the run enters the next non-empty block
+          if (!kCount) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        dx[c] = X0 + (float)c - A.x;
-        cadx[c] = A.z * dx[c];
-      }
+            for (int r = 0; r < 4; ++r)
+              part[k + tid][r] = make_float4(acc[2 * r].x, acc[2 * r].y, acc[2 * r + 1].x,
+                                             acc[2 * r + 1].y);
+          }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
-        const float dy = Y0 + (float)r - A.y;
-        const float bdy = A.w * dy;
-        const float cdy = fmaf(Bv.x * dy, dy, Bv.y);
+          for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+          do ++k;
+          while (ps[k + 1] <= i);
+          X0 = (float)(x0 + 4 * (k & 3));
+          Y0 = (float)(y0 + 4 * (k >> 2));
+        }
+        const int slot = flat[i];
+        const float4 A = sa[slot];
+        const float4 Bv = sb[slot];
+        const float2 npx = f2(-A.x);
+        const float2 dx01 = add2(make_float2(X0, X0 + 1.f), npx);
+        const float2 dx23 = add2(make_float2(X0 + 2.f, X0 + 3.f), npx);
+        const float2 ca = f2(A.z);
+        const float2 cadx01 = mul2(ca, dx01), cadx23 = mul2(ca, dx23);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float ev = fmaf(cadx[c] + bdy, dx[c], cdy);
+        for (int r = 0; r < 4; ++r) {
+          // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
+          const float dy = Y0 + (float)r - A.y;
+          const float2 bdy = f2(A.w * dy);
+          const float2 cdy = f2(fmaf(Bv.x * dy, dy, Bv.y));
+          const float2 e01 = fma2(add2(cadx01, bdy), dx01, cdy);
+          const float2 e23 = fma2(add2(cadx23, bdy), dx23, cdy);
           if (kCount) {
-            nkept += ev > l2tau;
+            nkept += (e01.x > l2tau) + (e01.y > l2tau) + (e23.x > l2tau) + (e23.y > l2tau);
           } else {
-            const float v = ex2_approx(ev);
-            if (ev > l2tau) acc[4 * r + c] += v;
+            // value on kept pairs (value > tau), zero elsewhere
+            acc[2 * r] = fma2(make_float2(ex2_approx(e01.x), ex2_approx(e01.y)),
+                              make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)), acc[2 * r]);
+            acc[2 * r + 1] =
+                fma2(make_float2(ex2_approx(e23.x), ex2_approx(e23.y)),
+                     make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)), acc[2 * r + 1]);
           }
         }
+        if (kCount) neval += 16;
       }
-      if (kCount) neval += 8;
-    }
-    // reduce-scatter over the 4 lanes sharing the rows (lane bit 1 picks the
-    // row, bit 0 the column pair): lane pp ends with row 2h + bit 1, columns
-    // 2 bit 0 + {0, 1}
+      if (!kCount) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const bool hi = (pp & 2) != 0;
-      const float send = hi ? acc[q] : acc[4 + q];
-      const float keep = hi ? acc[4 + q] : acc[q];
-      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        for (int r = 0; r < 4; ++r)
+          part[k + tid][r] =
+              make_float4(acc[2 * r].x, acc[2 * r].y, acc[2 * r + 1].x, acc[2 * r + 1].y);
+      }
     }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const bool hi = (pp & 1) != 0;
-      const float send = hi ? acc[q] : acc[2 + q];
-      const float keep = hi ? acc[2 + q] : acc[q];
-      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-    }
-    // the window's sums join the pixels' running sums (one owner per pixel
-    // per window, windows in list order; Kahan-compensated)
-    const int pl = (4 * (blk >> 2) + 2 * h + ((pp >> 1) & 1)) * kTile + 4 * (blk & 3) + 2 * (pp & 1);
-    if (!kCount) {
-      pix[pl] = kahan_add(pix[pl], acc[0]);
-      pix[pl + 1] = kahan_add(pix[pl + 1], acc[1]);
+    if (kCount) continue;
+    __syncthreads();
+    // each owned pixel sums the pieces of its block in thread order (runs
+    // in list order), then joins its running sum (Kahan)
+    {
+      const int pk = ps[ob], pe = ps[ob + 1];
+      if (pe > pk) {
+        // threads holding items pk and pe - 1
+        const int ulo = (kThreads * (pk + 1) + N - 1) / N - 1;
+        const int uhi = (kThreads * pe + N - 1) / N - 1;
+        float2 w = make_float2(0.f, 0.f);
+        for (int u = ulo; u <= uhi; ++u) {
+          if (((u * N) >> 7) == (((u + 1) * N) >> 7)) continue;  // empty run
+          const float2 v = reinterpret_cast<const float2 *>(&part[ob + u][ow >> 1])[ow & 1];
+          w.x += v.x;
+          w.y += v.y;
+        }
+        own0 = kahan_add(own0, w.x);
+        own1 = kahan_add(own1, w.y);
+      }
     }
   }
   if (kCount) {
@@ -213,12 +240,9 @@ __global__ void __launch_bounds__(kThreads, 12) raster_fwd_kernel(
     }
     return;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTile * kTile / 2; i += kThreads) {
-    const int r = (2 * i) / kTile, c = (2 * i) % kTile;
-    *reinterpret_cast<float2 *>(proj + ((int64_t)b * d + y0 + r) * d + x0 + c) =
-        make_float2(pix[2 * i].x - pix[2 * i].y, pix[2 * i + 1].x - pix[2 * i + 1].y);
-  }
+  const int px = x0 + 4 * (ob & 3) + 2 * (ow & 1), py = y0 + 4 * (ob >> 2) + (ow >> 1);
+  *reinterpret_cast<float2 *>(proj + ((int64_t)b * d + py) * d + px) =
+      make_float2(own0.x - own0.y, own1.x - own1.y);
 }
 
 cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
@@ -241,18 +265,25 @@ cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const uint16
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
+// kLpr lanes share one record (lane q of the group takes pixel rows
+// q * 4 / kLpr .. of every block of the record), so a round runs 32 / kLpr
+// records of neighbouring block counts; a warp window holds 32 * kPer
+// records.
+template <int kLpr, int kPer>
+__global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, const float *__restrict__ dproj, float *__restrict__ mom) {
   constexpr int kWarps = kThreads / 32;
-  constexpr int kPer = 2;            // records per lane per window
   constexpr int kWW = 32 * kPer;     // records per warp window
+  constexpr int kRpr = 32 / kLpr;    // records per round
+  constexpr int kRows = 4 / kLpr;    // pixel rows of a block per lane
   __shared__ float4 sg[16][4];  // g by 4x4 block: [block][row] = 4 pixels
   __shared__ float4 sa[kWarps][kWW], sb[kWarps][kWW];
   __shared__ uint32_t sj[kWarps][kWW];
   __shared__ unsigned short smask[kWarps][kWW];
-  __shared__ int hist[kWarps][17];
+  __shared__ int hist[kWarps][32];
+  __shared__ int next_win;
   const int nt = d / kTile, T = nt * nt;
   const int t = blockIdx.x, b = blockIdx.y;
   const int tx = t % nt, ty = t / nt;
@@ -264,6 +295,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     sg[4 * (r >> 2) + q][r & 3] =
         *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 + 4 * q);
   }
+  if (threadIdx.x == 0) next_win = kWarps;
   __syncthreads();
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
@@ -272,14 +304,18 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   const Rec *rb = rec + (int64_t)b * M;
   float *mb = mom + (int64_t)b * M * 6;
   int *h = hist[warp];
-  // warp w takes windows w, w + 4, ... of 64 records; no barrier couples the
-  // warps after the g tile is in place
-  for (int64_t base = s + kWW * warp; base < e; base += kWW * kWarps) {
+  const int gq = lane % kLpr;                                   // lane within the record's group
+  const unsigned gmask = ((1u << kLpr) - 1u) << (lane - gq);    // the group's lanes
+  const int row0 = gq * kRows;
+  // warp w takes window w first, then the next window not yet taken; no
+  // barrier couples the warps after the g tile is in place
+  int64_t base = s + kWW * warp;
+  while (base < e) {
     Rec r[kPer];
     uint32_t j[kPer];
     unsigned m[kPer];
     __syncwarp();  // previous window's reads are done
-    if (lane < 17) h[lane] = 0;
+    h[lane] = 0;
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
@@ -294,14 +330,18 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       atomicAdd(&h[__popc(m[q])], 1);
     }
     __syncwarp();
-    // exclusive scan of the count histogram, most blocks first
-    if (lane == 0) {
-      int run = 0;
-      for (int v = 16; v >= 0; --v) {
-        const int c = h[v];
-        h[v] = run;
-        run += c;
+    // exclusive scan of the count histogram, most blocks first: lane v gets
+    // the number of records with more than v blocks
+    {
+      const int c = h[lane];
+      int run = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_down_sync(0xffffffffu, run, o);
+        if (lane + o < 32) run += u;
       }
+      __syncwarp();
+      h[lane] = run - c;
     }
     __syncwarp();
 #pragma unroll
@@ -313,52 +353,73 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       smask[warp][pos] = (unsigned short)m[q];
     }
     __syncwarp();
-    // rounds of 32 records with neighbouring block counts
+    // rounds of 32 / kLpr records with neighbouring block counts
 #pragma unroll 1
-    for (int q = 0; q < kPer; ++q) {
-      const int slot = q * 32 + lane;
+    for (int q = 0; q < kWW / kRpr; ++q) {
+      const int slot = q * kRpr + lane / kLpr;
       const unsigned mk = smask[warp][slot];
-      if (!mk) continue;
+      if (!mk) continue;  // the whole group skips: the counts are sorted
       const float4 A = sa[warp][slot];
       const float4 Bv = sb[warp][slot];
-      const float ca = A.z, cb = A.w, cc = Bv.x, l2A = Bv.y;
-      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
+      const float2 ca2 = f2(A.z);
+      const float cb = A.w, cc = Bv.x, l2A = Bv.y;
+      float2 p0 = f2(0.f), p1 = f2(0.f), p2 = f2(0.f), p3 = f2(0.f), p4 = f2(0.f), p5 = f2(0.f);
       for (unsigned mm = mk; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
         const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
-        const float fy = (float)(y0 + 4 * (k >> 2)) - A.y;
+        const float fy = (float)(y0 + 4 * (k >> 2) + row0) - A.y;
+        const float2 dx01 = make_float2(fx, fx + 1.f);
+        const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
+        for (int rr = 0; rr < kRows; ++rr) {
           const float dy = fy + (float)rr;
-          const float bdy = cb * dy;
-          const float cdy = fmaf(cc * dy, dy, l2A);
-          const float4 g4 = sg[k][rr];
-          const float gq[4] = {g4.x, g4.y, g4.z, g4.w};
-          float a0 = 0.f, a1 = 0.f, a3 = 0.f;
-#pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            const float dx = fx + (float)c4;
-            const float ee = fmaf(fmaf(ca, dx, bdy), dx, cdy);
-            const float val = ex2_approx(ee);
-            const float gv = ee > l2tau ? gq[c4] * val : 0.f;
-            a0 += gv;
-            const float tt = gv * dx;
-            a1 += tt;
-            a3 = fmaf(tt, dx, a3);
-          }
-          m0 += a0;
-          m1 += a1;
-          m2 = fmaf(dy, a0, m2);
-          m3 += a3;
-          m4 = fmaf(dy, a1, m4);
-          m5 = fmaf(dy * dy, a0, m5);
+          const float2 bdy = f2(cb * dy);
+          const float2 cdy = f2(fmaf(cc * dy, dy, l2A));
+          // e = (ca dx + cb dy) dx + cc dy^2 + l2A, as in the forward's terms
+          const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
+          const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
+          const float4 g4 = sg[k][row0 + rr];
+          // g * value on kept pairs (value > tau), zero elsewhere
+          const float2 gm01 = mul2(make_float2(g4.x, g4.y),
+                                   make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
+          const float2 gm23 = mul2(make_float2(g4.z, g4.w),
+                                   make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)));
+          const float2 gv01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
+          const float2 gv23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
+          const float2 s0 = add2(gv01, gv23);
+          const float2 t01 = mul2(gv01, dx01), t23 = mul2(gv23, dx23);
+          const float2 s1 = add2(t01, t23);
+          p3 = fma2(t01, dx01, p3);
+          p3 = fma2(t23, dx23, p3);
+          p0 = add2(p0, s0);
+          p1 = add2(p1, s1);
+          const float2 dy2 = f2(dy);
+          p2 = fma2(s0, dy2, p2);
+          p4 = fma2(s1, dy2, p4);
+          p5 = fma2(s0, f2(dy * dy), p5);
         }
       }
-      float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[warp][slot] * 6);
-      atomicAdd(mo + 0, make_float2(m0, m1));
-      atomicAdd(mo + 1, make_float2(m2, m3));
-      atomicAdd(mo + 2, make_float2(m4, m5));
+      float m0 = p0.x + p0.y, m1 = p1.x + p1.y, m2 = p2.x + p2.y;
+      float m3 = p3.x + p3.y, m4 = p4.x + p4.y, m5 = p5.x + p5.y;
+#pragma unroll
+      for (int o = 1; o < kLpr; o <<= 1) {
+        m0 += __shfl_xor_sync(gmask, m0, o);
+        m1 += __shfl_xor_sync(gmask, m1, o);
+        m2 += __shfl_xor_sync(gmask, m2, o);
+        m3 += __shfl_xor_sync(gmask, m3, o);
+        m4 += __shfl_xor_sync(gmask, m4, o);
+        m5 += __shfl_xor_sync(gmask, m5, o);
+      }
+      if (gq == 0) {
+        float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[warp][slot] * 6);
+        atomicAdd(mo + 0, make_float2(m0, m1));
+        atomicAdd(mo + 1, make_float2(m2, m3));
+        atomicAdd(mo + 2, make_float2(m4, m5));
+      }
     }
+    int wn = 0;
+    if (lane == 0) wn = atomicAdd(&next_win, 1);
+    base = s + (int64_t)kWW * __shfl_sync(0xffffffffu, wn, 0);
   }
 }
 
@@ -367,8 +428,8 @@ cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const uint16
                               float l2tau, const float *dproj, float *mom, cudaStream_t st) {
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
-  raster_bwd_kernel<<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d, l2tau,
-                                               dproj, mom);
+  raster_bwd_kernel<kBwdLanes, kBwdPer><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start,
+                                                                  cap, M, d, l2tau, dproj, mom);
   return cudaGetLastError();
 }
 
