@@ -207,7 +207,11 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->bin.tcnt, (size_t)g.max_B * nchT * c->T) &&
             alloc(c, &c->bin.tile_start, (size_t)g.max_B * c->T + 1) &&
             alloc(c, &c->bin.list, (size_t)c->cfg.max_pairs) &&
-            alloc(c, &c->bin.lmask, (size_t)c->cfg.max_pairs) && alloc(c, &c->mom, BM * 6) &&
+            alloc(c, &c->bin.lmask, (size_t)c->cfg.max_pairs) &&
+            alloc(c, &c->bin.hits, (size_t)c->cfg.max_pairs) &&
+            alloc(c, &c->bin.chunk_base, (size_t)g.max_B * nchT) &&
+            alloc(c, &c->bin.chunk_n, (size_t)g.max_B * nchT) && alloc(c, &c->bin.hit_ctr, 1) &&
+            alloc(c, &c->mom, BM * 6) &&
             alloc(c, &c->part, (size_t)c->nbg * g.max_M * kNpar) &&
             alloc(c, &c->proj, (size_t)g.max_B * d * d) &&
             alloc(c, &c->dproj, (size_t)g.max_B * d * d) &&

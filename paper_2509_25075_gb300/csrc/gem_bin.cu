@@ -12,7 +12,9 @@
 // across chunks, then scatter with a rank inside the chunk that preserves
 // input order.  The result is deterministic: no position depends on thread
 // timing.  Each list entry also gets the mask of the 4x4 pixel blocks of
-// its tile that the Gaussian's region above tau meets.
+// its tile that the Gaussian's region above tau meets.  The tile count pass
+// does all the geometry (candidate tiles, exact tile tests, block masks) and
+// records each hit; the scatter pass only ranks and writes them.
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -260,28 +262,88 @@ __device__ __forceinline__ int candidate_owner(const ChunkStage &S, int k, int t
 }
 
 // Per chunk of 256 Gaussians (depth order) of image b: how many hit each
-// tile.  Written transposed, tcnt[b][t][c], so that each tile's column is
-// contiguous for the scan.
-__global__ void __launch_bounds__(kChunkT) tile_count_kernel(const Rec *__restrict__ rec,
-                                                             const uint32_t *__restrict__ perm,
-                                                             int64_t M, int d, float l2tau,
-                                                             int nch, uint32_t *__restrict__ tcnt) {
+// tile, written transposed, tcnt[b][t][c], so that each tile's column is
+// contiguous for the scan; and every hit, (slot o in the chunk, tile, 4x4-block
+// mask), in a run of hits[] claimed from a shared cursor, so that the scatter
+// pass repeats none of the geometry.  The run's contents and layout (threads
+// in order, each thread's candidates in order) do not depend on timing; only
+// where it starts does.
+__device__ __forceinline__ uint64_t pack_hit(int o, int t, unsigned mask) {
+  return (uint64_t)o | ((uint64_t)t << 8) | ((uint64_t)mask << 24);
+}
+
+__global__ void __launch_bounds__(kChunkT) tile_count_kernel(
+    const Rec *__restrict__ rec, const uint32_t *__restrict__ perm, int64_t M, int d,
+    float l2tau, int nch, uint32_t *__restrict__ tcnt, BinScratch bs) {
   extern __shared__ uint32_t tc[];
   __shared__ ChunkStage S;
+  __shared__ uint32_t hbits[kOwnerCap / 32];  // hit flag of each candidate (when they fit)
+  __shared__ int wh[kChunkT / 32];
+  __shared__ int64_t run_base;
   const int c = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nt = d / kTile, T = nt * nt;
   for (int i = threadIdx.x; i < T; i += blockDim.x) tc[i] = 0;
   stage_chunk(S, rec, perm, M, b, c, d, l2tau);
   const int total = S.off[kChunkT];
-  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+  const bool keep_bits = total <= kOwnerCap;
+  int nh = 0;
+  for (int k0 = 0; k0 < total; k0 += kChunkT) {
+    const int k = k0 + threadIdx.x;
+    bool hit = false;
+    if (k < total) {
+      const int o = candidate_owner(S, k, total);
+      int tx, ty;
+      candidate_tile(S, o, k - S.off[o], tx, ty);
+      hit = tile_hit(S.ell[o], tx * kTile, ty * kTile);
+      if (hit) {
+        atomicAdd(&tc[ty * nt + tx], 1u);
+        ++nh;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (keep_bits && lane == 0 && k0 + warp * 32 < total) hbits[(k0 >> 5) + warp] = bal;
+  }
+  // this thread's hits go after those of lower threads
+  int inc = nh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wh[warp] = inc;
+  __syncthreads();
+  int before = inc - nh, H = 0;
+#pragma unroll
+  for (int w = 0; w < kChunkT / 32; ++w) {
+    if (w < warp) before += wh[w];
+    H += wh[w];
+  }
+  if (threadIdx.x == 0) {
+    const int64_t base = (int64_t)atomicAdd(bs.hit_ctr, (unsigned long long)H);
+    run_base = base;
+    bs.chunk_base[(int64_t)b * nch + c] = base;
+    bs.chunk_n[(int64_t)b * nch + c] = (uint32_t)H;
+  }
+  __syncthreads();
+  int64_t dst = run_base + before;
+  for (int k0 = 0; k0 < total && nh > 0; k0 += kChunkT) {
+    const int k = k0 + threadIdx.x;
+    if (k >= total) break;
     const int o = candidate_owner(S, k, total);
     int tx, ty;
     candidate_tile(S, o, k - S.off[o], tx, ty);
-    if (tile_hit(S.ell[o], tx * kTile, ty * kTile)) atomicAdd(&tc[ty * nt + tx], 1u);
+    const bool hit = keep_bits ? ((hbits[k >> 5] >> (k & 31)) & 1u) != 0
+                               : tile_hit(S.ell[o], tx * kTile, ty * kTile);
+    if (!hit) continue;
+    if (dst < bs.cap)
+      bs.hits[dst] = pack_hit(o, ty * nt + tx, block_mask16(S.ell[o], tx * kTile, ty * kTile));
+    ++dst;
+    --nh;
   }
   __syncthreads();
-  uint32_t *dst = tcnt + (int64_t)b * T * nch + c;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) dst[(int64_t)i * nch] = tc[i];
+  uint32_t *out = tcnt + (int64_t)b * T * nch + c;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) out[(int64_t)i * nch] = tc[i];
 }
 
 // One warp per (image, tile): exclusive scan of the chunk counts in place;
@@ -350,47 +412,42 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
   }
 }
 
-// Scatter: Gaussian i of the chunk (depth order) sets bit i in the bitmap of
-// every tile it hits; its position in a tile's list is the tile's start,
-// plus the chunk's offset for that tile, plus the number of lower bits set.
-// Beside the Gaussian's index the entry stores its 4x4-block mask.  The
-// chunk's (Gaussian, candidate tile) pairs are spread over the threads.
+// Scatter: the chunk's hits (from the count pass) set bit o in the bitmap of
+// their tile; a hit's place in its tile's list is the tile's start, plus the
+// chunk's offset for that tile, plus the number of lower bits set (so the
+// list keeps the chunk's depth order).  Beside the Gaussian's index the
+// entry stores its 4x4-block mask.
 __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
-    const Rec *__restrict__ rec, const uint32_t *__restrict__ perm, int64_t M, int d,
-    float l2tau, int nch, const uint32_t *__restrict__ tcnt,
-    const int64_t *__restrict__ tile_start, int64_t cap, uint32_t *__restrict__ list,
-    uint16_t *__restrict__ lmask) {
+    const uint32_t *__restrict__ perm, int64_t M, int d, int nch,
+    const uint32_t *__restrict__ tcnt, const int64_t *__restrict__ tile_start, BinScratch bs) {
   extern __shared__ uint32_t bm[];  // [T][8]
-  __shared__ ChunkStage S;
   const int c = blockIdx.x, b = blockIdx.y;
   const int nt = d / kTile, T = nt * nt;
   for (int i = threadIdx.x; i < T * 8; i += blockDim.x) bm[i] = 0;
-  stage_chunk(S, rec, perm, M, b, c, d, l2tau);
-  const int total = S.off[kChunkT];
-  for (int k = threadIdx.x; k < total; k += blockDim.x) {
-    const int o = candidate_owner(S, k, total);
-    int tx, ty;
-    candidate_tile(S, o, k - S.off[o], tx, ty);
-    if (tile_hit(S.ell[o], tx * kTile, ty * kTile))
-      atomicOr(&bm[(ty * nt + tx) * 8 + (o >> 5)], 1u << (o & 31));
+  const int64_t hb = bs.chunk_base[(int64_t)b * nch + c];
+  const int64_t hn = min((int64_t)bs.chunk_n[(int64_t)b * nch + c], max(bs.cap - hb, (int64_t)0));
+  const int H = (int)hn;
+  __syncthreads();
+  const uint64_t *hr = bs.hits + hb;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    const uint64_t h = hr[i];
+    const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
+    atomicOr(&bm[t * 8 + (o >> 5)], 1u << (o & 31));
   }
   __syncthreads();
   const uint32_t *coff = tcnt + (int64_t)b * T * nch + c;
-  for (int k = threadIdx.x; k < total; k += blockDim.x) {
-    const int o = candidate_owner(S, k, total);
-    int tx, ty;
-    candidate_tile(S, o, k - S.off[o], tx, ty);
-    const int t = ty * nt + tx;
+  const int64_t r0 = (int64_t)c * kChunkT;
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    const uint64_t h = hr[i];
+    const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
     const uint32_t *bw = bm + t * 8;
     const int word = o >> 5;
-    const uint32_t bit = 1u << (o & 31);
-    if (!(bw[word] & bit)) continue;
-    uint32_t rank = __popc(bw[word] & (bit - 1u));
+    uint32_t rank = __popc(bw[word] & ((1u << (o & 31)) - 1u));
     for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk]);
     const int64_t pos = tile_start[(int64_t)b * T + t] + coff[(int64_t)t * nch] + rank;
-    if (pos < cap) {
-      list[pos] = S.j[o];
-      lmask[pos] = (uint16_t)block_mask16(S.ell[o], tx * kTile, ty * kTile);
+    if (pos < bs.cap) {
+      bs.list[pos] = perm ? perm[(int64_t)b * M + r0 + o] : (uint32_t)(r0 + o);
+      bs.lmask[pos] = (uint16_t)(h >> 24);
     }
   }
 }
@@ -434,13 +491,13 @@ cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, in
   int nch = (int)bin_chunks_tiles(M);
   dim3 g(nch, B);
   int cnt_smem = T * (int)sizeof(uint32_t);
-  tile_count_kernel<<<g, 256, cnt_smem, st>>>(rec, perm, M, d, l2tau, nch, s.tcnt);
+  if ((e = cudaMemsetAsync(s.hit_ctr, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  tile_count_kernel<<<g, 256, cnt_smem, st>>>(rec, perm, M, d, l2tau, nch, s.tcnt, s);
   int64_t ncols = (int64_t)B * T;
   tile_scan_cols_kernel<<<(unsigned)((ncols + 7) / 8), 256, 0, st>>>(s.tcnt, nch, ncols,
                                                                       s.tile_start);
   scan_tiles_kernel<<<1, 1024, 0, st>>>(s.tile_start, ncols, s.cap, s.status);
-  tile_scatter_kernel<<<g, 256, tile_smem_bytes(d), st>>>(rec, perm, M, d, l2tau, nch, s.tcnt,
-                                                         s.tile_start, s.cap, s.list, s.lmask);
+  tile_scatter_kernel<<<g, 256, tile_smem_bytes(d), st>>>(perm, M, d, nch, s.tcnt, s.tile_start, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   *perm_out = perm;
   return cudaSuccess;

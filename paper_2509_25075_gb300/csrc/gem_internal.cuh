@@ -344,6 +344,11 @@ struct BinScratch {
   int64_t *tile_start;     // [B*T + 1]
   uint32_t *list;          // [cap] Gaussian index per entry
   uint16_t *lmask;         // [cap] 4x4-block mask per entry
+  uint64_t *hits;          // [cap] (slot in chunk, tile, 4x4-block mask) of every hit,
+                           // grouped by chunk (written by the count pass)
+  int64_t *chunk_base;     // [B][nchT] where a chunk's hits start in hits[]
+  uint32_t *chunk_n;       // [B][nchT] how many hits the chunk has
+  unsigned long long *hit_ctr;  // [1] hits[] allocation cursor
   int64_t cap;
   int *status;
 };

@@ -23,8 +23,9 @@
 //     not yet taken), sorts the window by block count and runs it in rounds
 //     of 16 records with neighbouring counts, two lanes per record (two
 //     pixel rows of each block each): the lanes walk the record's blocks and
-//     accumulate six moments of g * value in registers (packed float
-//     pairs), then add their halves.  No barrier couples the warps.  a6 turns
+//     accumulate six moments of g * value in registers (per row: the sums
+//     of w, w dx, w dx^2 in packed float pairs, weighted by dy), then add
+//     their halves.  No barrier couples the warps.  a6 turns
 //     the moments into parameter gradients.  One set of vector atomics per
 //     (tile, Gaussian) goes to global memory.
 #include "gem_internal.cuh"
@@ -311,7 +312,6 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   // barrier couples the warps after the g tile is in place
   int64_t base = s + kWW * warp;
   while (base < e) {
-    Rec r[kPer];
     uint32_t j[kPer];
     unsigned m[kPer];
     __syncwarp();  // previous window's reads are done
@@ -324,7 +324,6 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       m[q] = 0;
       if (i < e) {
         j[q] = list[i];
-        r[q] = rb[j[q]];
         m[q] = lmask[i];
       }
       atomicAdd(&h[__popc(m[q])], 1);
@@ -347,8 +346,11 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int pos = atomicAdd(&h[__popc(m[q])], 1);
-      sa[warp][pos] = r[q].a;
-      sb[warp][pos] = r[q].b;
+      if (m[q]) {
+        const Rec r = rb[j[q]];
+        sa[warp][pos] = r.a;
+        sb[warp][pos] = r.b;
+      }
       sj[warp][pos] = j[q];
       smask[warp][pos] = (unsigned short)m[q];
     }
@@ -363,13 +365,14 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       const float4 Bv = sb[warp][slot];
       const float2 ca2 = f2(A.z);
       const float cb = A.w, cc = Bv.x, l2A = Bv.y;
-      float2 p0 = f2(0.f), p1 = f2(0.f), p2 = f2(0.f), p3 = f2(0.f), p4 = f2(0.f), p5 = f2(0.f);
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
       for (unsigned mm = mk; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
         const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
         const float fy = (float)(y0 + 4 * (k >> 2) + row0) - A.y;
         const float2 dx01 = make_float2(fx, fx + 1.f);
         const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
+        const float2 dxx01 = mul2(dx01, dx01), dxx23 = mul2(dx23, dx23);
 #pragma unroll
         for (int rr = 0; rr < kRows; ++rr) {
           const float dy = fy + (float)rr;
@@ -379,28 +382,26 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
           const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
           const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
           const float4 g4 = sg[k][row0 + rr];
-          // g * value on kept pairs (value > tau), zero elsewhere
+          // w = g * value on kept pairs (value > tau), zero elsewhere
           const float2 gm01 = mul2(make_float2(g4.x, g4.y),
                                    make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
           const float2 gm23 = mul2(make_float2(g4.z, g4.w),
                                    make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)));
-          const float2 gv01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
-          const float2 gv23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
-          const float2 s0 = add2(gv01, gv23);
-          const float2 t01 = mul2(gv01, dx01), t23 = mul2(gv23, dx23);
-          const float2 s1 = add2(t01, t23);
-          p3 = fma2(t01, dx01, p3);
-          p3 = fma2(t23, dx23, p3);
-          p0 = add2(p0, s0);
-          p1 = add2(p1, s1);
-          const float2 dy2 = f2(dy);
-          p2 = fma2(s0, dy2, p2);
-          p4 = fma2(s1, dy2, p4);
-          p5 = fma2(s0, f2(dy * dy), p5);
+          const float2 w01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
+          const float2 w23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
+          // the row's sums of w, w dx and w dx^2, then weighted by dy
+          const float2 s0 = add2(w01, w23);
+          const float2 s1 = fma2(w23, dx23, mul2(w01, dx01));
+          const float2 s2 = fma2(w23, dxx23, mul2(w01, dxx01));
+          const float r0 = s0.x + s0.y, r1 = s1.x + s1.y, r2 = s2.x + s2.y;
+          m0 += r0;
+          m1 += r1;
+          m3 += r2;
+          m2 = fmaf(r0, dy, m2);
+          m4 = fmaf(r1, dy, m4);
+          m5 = fmaf(r0 * dy, dy, m5);
         }
       }
-      float m0 = p0.x + p0.y, m1 = p1.x + p1.y, m2 = p2.x + p2.y;
-      float m3 = p3.x + p3.y, m4 = p4.x + p4.y, m5 = p5.x + p5.y;
 #pragma unroll
       for (int o = 1; o < kLpr; o <<= 1) {
         m0 += __shfl_xor_sync(gmask, m0, o);
