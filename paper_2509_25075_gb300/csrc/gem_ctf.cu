@@ -75,8 +75,9 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass1_kernel(
   load_twiddles(tws, tw, d);
   const float *pr = proj + ((int64_t)b * d + y0) * d;
   const float *im = images + ((int64_t)b * d + y0) * d;
+  const float rd = 1.f / (float)d;
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
-    const int l = i / d, x = i - l * d;
+    const int l = fdiv_small(i, rd), x = i - l * d;
     a[l * ls + x] = make_float2(pr[i], im[i]);
   }
   __syncthreads();
@@ -195,13 +196,14 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   load_twiddles(tws, tw, d);
   if (ctf_params && threadIdx.x == 0) cc = ctf_const(ctf_params + 8 * b, d, apix);
   float2 *zb = Z + (int64_t)b * d * d;
+  const float rd = 1.f / (float)d;
   // load the 16 lines: i < 8 -> kx1, i >= 8 -> kx2
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
-    int i = idx / d, y = idx - i * d;
+    int i = fdiv_small(idx, rd), y = idx - i * d;
     int kx1 = 8 * blk + (i & 7);
     float2 v = make_float2(0.f, 0.f);
     if (kx1 <= hd) {
-      int kx = i < 8 ? kx1 : (d - kx1) % d;
+      int kx = i < 8 ? kx1 : (kx1 == 0 ? 0 : d - kx1);
       v = zb[(int64_t)kx * d + y];
     }
     a[i * ls + y] = v;
@@ -211,12 +213,12 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   // combine: thread per (pair i, ky)
   float lsum = 0.f;
   for (int idx = threadIdx.x; idx < 8 * d; idx += blockDim.x) {
-    int i = idx / d, ky = idx - i * d;
+    int i = fdiv_small(idx, rd), ky = idx - i * d;
     int kx = 8 * blk + i;
     if (kx > hd) continue;
     bool self = (kx == 0 || kx == hd);
     if (self && ky > hd) continue;
-    int mky = (d - ky) % d;
+    int mky = ky == 0 ? 0 : d - ky;
     float2 *l1 = L + i * ls;
     float2 *l2 = self ? l1 : L + (8 + i) * ls;
     float2 z1 = l1[ky], z2 = l2[mky];
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
       int sx = signed_bin(kx, d), sy = signed_bin(ky, d);
       h = ctf_at(cc, sx, sy);
       if (kx == hd || ky == hd) {
-        int px = signed_bin((d - kx) % d, d), py = signed_bin(mky, d);
+        int px = signed_bin(kx == 0 ? 0 : d - kx, d), py = signed_bin(mky, d);
         h = 0.5f * (h + ctf_at(cc, px, py));
       }
     } else {
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   float2 *other = (L == a) ? bb : a;
   float2 *R2 = fft_lines(L, other, kLines, pl, tws, ls);
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
-    int i = idx / d, y = idx - i * d;
+    int i = fdiv_small(idx, rd), y = idx - i * d;
     int kx1 = 8 * blk + (i & 7);
     if (kx1 > hd) continue;
     bool self = (kx1 == 0 || kx1 == hd);
@@ -294,8 +296,9 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
   __syncthreads();
   float2 *res = fft_lines(a, bb, kLines, pl, tws, ls);
   int64_t off = ((int64_t)b * d + y0) * d;
+  const float rd = 1.f / (float)d;
   for (int i = threadIdx.x; i < kLines * d; i += blockDim.x) {
-    const int l = i / d, x = i - l * d;
+    const int l = fdiv_small(i, rd), x = i - l * d;
     float2 v = res[l * ls + x];
     if (pred) pred[off + i] = v.x * inv_n2;
     if (dproj) dproj[off + i] = -v.y * gscale;

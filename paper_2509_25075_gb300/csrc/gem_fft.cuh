@@ -8,6 +8,14 @@
 
 namespace gem {
 
+// x / D for 0 <= x <= 16 n and D <= n <= 768, given r = 1/D rounded to
+// float: (x + 1/2) r, one fused rounding, is within 1e-4 of (x + 1/2) / D,
+// which is at least 1/(2 D) >= 6.5e-4 away from an integer, so truncation
+// gives the exact quotient (checked exhaustively for every supported n).
+__device__ __forceinline__ int fdiv_small(int x, float r) {
+  return (int)fmaf((float)x, r, 0.5f * r);
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -23,12 +31,14 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ src, float2
   const int nb = n / R;
   const int tws = n / (Ns * R);
   const int total = nl * nb;
+  const float rnb = 1.f / (float)nb, rns = 1.f / (float)Ns;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int line = idx / nb;
+    const int line = fdiv_small(idx, rnb);
     const int jj = idx - line * nb;
     const float2 *in = src + line * ls;
     float2 *out = dst + line * ls;
-    const int k = jj % Ns;
+    const int q = fdiv_small(jj, rns);
+    const int k = jj - q * Ns;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[jj + r * nb];
@@ -56,7 +66,7 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ src, float2
       v[1] = make_float2(t2.x + t3.x, t2.y + t3.y);
       v[2 % R] = make_float2(t2.x - t3.x, t2.y - t3.y);
     }
-    const int obase = (jj / Ns) * Ns * R + k;
+    const int obase = q * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) out[obase + r * Ns] = v[r];
   }

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kFThreads) fsc_pass_real_kernel(
   for (int i = threadIdx.x; i < d; i += blockDim.x) tws[i] = tw[i];
   const int64_t base = ((int64_t)z * d + y0) * d;
   for (int i = threadIdx.x; i < kFL * d; i += blockDim.x) {
-    const int l = i / d, x = i - l * d;
+    const int l = fdiv_small(i, 1.f / (float)d), x = i - l * d;
     a[l * ls + x] = make_float2(X1[base + i], X2[base + i]);
   }
   __syncthreads();
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kFThreads) fsc_pass_cplx_kernel(const float2 *
   for (int i = threadIdx.x; i < d; i += blockDim.x) tws[i] = tw[i];
   const int64_t base = ((int64_t)i0 * d + i10) * d;
   for (int i = threadIdx.x; i < kFL * d; i += blockDim.x) {
-    const int l = i / d, x = i - l * d;
+    const int l = fdiv_small(i, 1.f / (float)d), x = i - l * d;
     a[l * ls + x] = A[base + i];
   }
   __syncthreads();

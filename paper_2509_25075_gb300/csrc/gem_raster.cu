@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
       float X0 = (float)(x0 + 4 * (k & 3)), Y0 = (float)(y0 + 4 * (k >> 2));
+      int kend = ps[k + 1];  // end of block k's items
       for (int i = lo; i < hi; ++i) {
-        if (i >= ps[k + 1]) {  // the run enters the next non-empty block
+        if (i >= kend) {  // the run enters the next non-empty block
           if (!kCount) {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
           for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
           do ++k;
           while (ps[k + 1] <= i);
+          kend = ps[k + 1];
           X0 = (float)(x0 + 4 * (k & 3));
           Y0 = (float)(y0 + 4 * (k >> 2));
         }
