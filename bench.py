@@ -58,10 +58,10 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "293f148a62e6e98e",
+    "source_sha256_16": "3d5ee3fc58c51697",
     "workload": "A2",
-    "raster_fwd": 262.171904e6 + 17.494016e6,
-    "raster_bwd": 497.048576e6 + 141.650944e6,
+    "raster_fwd": 262.734592e6 + 17.832704e6,
+    "raster_bwd": 421.471744e6 + 95.915264e6,
 }
 
 
