@@ -8,7 +8,7 @@
 // evaluations per block it touches, instead of 256 per tile.
 //
 // a3: Eq. render restricted by Eq. accu.  Records are staged 256 at a time
-//     (a window); ballots lay the window's (block, record) items out block
+//     (a window; only the 24 bytes the evaluation reads); ballots lay the window's (block, record) items out block
 //     after block, each block's records in list order.  The items are cut
 //     into 128 equal runs, one per thread, so every thread does the same
 //     amount of work whatever the blocks' list lengths.  A thread evaluates
@@ -43,7 +43,7 @@ __device__ __forceinline__ float2 kahan_add(float2 s, float x) {
 constexpr int kSub = 2;                // forward: records staged per thread per window
 constexpr int kWin = kThreads * kSub;  // records staged per window
 static_assert(kThreads == 128, "the forward splits items with shifts by 7");
-constexpr int kFwdMinBlocks = 9;      // forward: CTAs per SM (its shared memory allows 9)
+constexpr int kFwdMinBlocks = 9;      // forward: CTAs per SM (10, with fewer registers, ran slower)
 constexpr int kBwdLanes = 2;          // backward: lanes sharing one record
 constexpr int kBwdPer = 4;            // backward: records per lane per warp window
 
@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
     unsigned long long *__restrict__ kept) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kPieces = 16 + kThreads - 1;
-  __shared__ float4 sa[kWin], sb[kWin];
+  __shared__ float4 sa[kWin];                         // px, py, ca, cb
+  __shared__ float2 sb[kWin];                         // cc, log2 A
   __shared__ unsigned char flat[16 * kWin];           // staged slot of each (block, record) item,
                                                       // blocks in order, records in list order
   __shared__ unsigned short wcnt[kSub][kWarps][16];  // per sub-window, warp, block: how many
@@ -91,10 +92,12 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
       const int slot = u * kThreads + tid;
       m[u] = 0;
       if (slot < n) {
-        const Rec r = rb[list[base + slot]];
+        const Rec *rp = rb + list[base + slot];
+        const float4 ra = rp->a;
+        const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
         m[u] = lmask[base + slot];
-        sa[slot] = r.a;
-        sb[slot] = r.b;
+        sa[slot] = ra;
+        sb[slot] = rbv;
       }
       unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
 #pragma unroll
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
         }
         const int slot = flat[i];
         const float4 A = sa[slot];
-        const float4 Bv = sb[slot];
+        const float2 Bv = sb[slot];
         const float2 npx = f2(-A.x);
         const float2 dx01 = add2(make_float2(X0, X0 + 1.f), npx);
         const float2 dx23 = add2(make_float2(X0 + 2.f, X0 + 3.f), npx);
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   constexpr int kRpr = 32 / kLpr;    // records per round
   constexpr int kRows = 4 / kLpr;    // pixel rows of a block per lane
   __shared__ float4 sg[16][4];  // g by 4x4 block: [block][row] = 4 pixels
-  __shared__ float4 sa[kWarps][kWW], sb[kWarps][kWW];
+  __shared__ float4 sa[kWarps][kWW];  // px, py, ca, cb
+  __shared__ float2 sb[kWarps][kWW];  // cc, log2 A
   __shared__ uint32_t sj[kWarps][kWW];
   __shared__ unsigned short smask[kWarps][kWW];
   __shared__ int hist[kWarps][32];
@@ -349,9 +353,9 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     for (int q = 0; q < kPer; ++q) {
       const int pos = atomicAdd(&h[__popc(m[q])], 1);
       if (m[q]) {
-        const Rec r = rb[j[q]];
-        sa[warp][pos] = r.a;
-        sb[warp][pos] = r.b;
+        const Rec *rp = rb + j[q];
+        sa[warp][pos] = rp->a;
+        sb[warp][pos] = *reinterpret_cast<const float2 *>(&rp->b);
       }
       sj[warp][pos] = j[q];
       smask[warp][pos] = (unsigned short)m[q];
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       const unsigned mk = smask[warp][slot];
       if (!mk) continue;  // the whole group skips: the counts are sorted
       const float4 A = sa[warp][slot];
-      const float4 Bv = sb[warp][slot];
+      const float2 Bv = sb[warp][slot];
       const float2 ca2 = f2(A.z);
       const float cb = A.w, cc = Bv.x, l2A = Bv.y;
       float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
