@@ -141,15 +141,20 @@ struct CtfConst {
 };
 
 __device__ CtfConst ctf_const(const float *__restrict__ prm, int d, float apix) {
-  double dU = prm[0], dV = prm[1], ang = prm[2], volt = (double)prm[3] * 1e3;
+  double dU = prm[0], dV = prm[1], volt = (double)prm[3] * 1e3;
   double cs = (double)prm[4] * 1e7, w = prm[5], phase = prm[6], bf = prm[7];
   double lam = 12.2643247 / sqrt(volt * (1.0 + 0.978466e-6 * volt));
   double cf = 1.0 / ((double)d * apix * (double)d * apix);
   double mean = 0.5 * (dU + dV), half = 0.5 * (dU - dV);
+  // the astigmatism terms reach a fraction of a turn at Nyquist, so the
+  // angle's cosine and sine need float accuracy only (kept off the slow
+  // double-precision path, which this single thread runs while its CTA waits)
+  float s2a, c2a;
+  sincosf(2.f * prm[2], &s2a, &c2a);
   CtfConst c;
   c.c1 = ff_split(0.5 * lam * mean * cf);
-  c.c2 = ff_split(0.5 * lam * half * cos(2.0 * ang) * cf);
-  c.c3 = ff_split(0.5 * lam * half * sin(2.0 * ang) * cf);
+  c.c2 = ff_split(0.5 * lam * half * (double)c2a * cf);
+  c.c3 = ff_split(0.5 * lam * half * (double)s2a * cf);
   c.c4 = ff_split(-0.25 * cs * lam * lam * lam * cf * cf);
   c.ph = ff_split(phase / (2.0 * 3.14159265358979323846));
   c.sw = (float)sqrt(1.0 - w * w);
