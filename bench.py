@@ -395,8 +395,13 @@ def main():
     traffic = None
     if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] and w.name == CAPTURED_TRAFFIC["workload"]:
         traffic = CAPTURED_TRAFFIC[dom]
+    other = "raster_bwd" if dom == "raster_fwd" else "raster_fwd"
+    o_peak = sms * min(FP32_PER_CLK_PER_SM / FP32_OPS_PER_KEPT_PAIR[other], EX2_PER_CLK_PER_SM) * mhz * 1e6 / 1e9
+    o_ach = kept / (per_stage[other] / 1e3) / 1e9
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "other_rasteriser": {"kernel": other, "achieved": o_ach, "peak": o_peak, "frac": o_ach / o_peak,
+                                 "traffic": CAPTURED_TRAFFIC[other] if traffic is not None else None},
             "peak_note": f"{sms} SMs x min({FP32_PER_CLK_PER_SM} FP32 lanes / {ops} FMA-pipe ops per kept "
                          f"pair, {EX2_PER_CLK_PER_SM} ex2) per clock x {mhz:.0f} MHz median SM clock under load",
             "sfu_only": {"peak": peak_sfu, "frac": achieved / peak_sfu,
