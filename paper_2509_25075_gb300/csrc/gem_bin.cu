@@ -80,12 +80,13 @@ __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *__restrict__ 
   for (int c = 0; c < nch; ++c) col[(int64_t)c * 256] += base;
 }
 
-// Lanes of the warp holding the same 9-bit value: one ballot per bit
+// Lanes of the warp holding the same kBits-bit value: one ballot per bit
 // (faster here than a match instruction).
+template <int kBits>
 __device__ __forceinline__ unsigned same_value_lanes(int v) {
   unsigned p = 0xffffffffu;
 #pragma unroll
-  for (int bit = 0; bit < 9; ++bit) {
+  for (int bit = 0; bit < kBits; ++bit) {
     const bool set = (v >> bit) & 1;
     const unsigned bal = __ballot_sync(0xffffffffu, set);
     p &= set ? bal : ~bal;
@@ -112,13 +113,10 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
   const int64_t cbase = (int64_t)c * kChunkD + warp * kPer;
   const int64_t ibase = (int64_t)b * M;
   const unsigned lt = (1u << lane) - 1u;
-  // per-warp digit counts (tail lanes get digits that never match)
+  // per-warp digit counts (order does not matter here: plain increments)
   for (int r = 0; r < kPer / 32; ++r) {
     int64_t e = cbase + r * 32 + lane;
-    int dig = e < M ? (int)digit_of<kPass>(key, packed, ibase + e) : 256 + lane;
-    unsigned peers = same_value_lanes(dig);
-    if (dig < 256 && lane == __ffs(peers) - 1) wc[warp][dig] += __popc(peers);
-    __syncwarp();
+    if (e < M) atomicAdd(&wc[warp][digit_of<kPass>(key, packed, ibase + e)], 1u);
   }
   __syncthreads();
   // exclusive prefix over warps, plus the chunk's offset
@@ -148,7 +146,10 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
         word &= 0xffffffu;
       }
     }
-    unsigned peers = same_value_lanes(dig);
+    // a full round has no tail lanes, so the 8 digit bits decide alone;
+    // the last round of a chunk also tells tail lanes (digit 256 + lane) apart
+    const bool full = cbase + r * 32 + 31 < M;
+    unsigned peers = full ? same_value_lanes<8>(dig) : same_value_lanes<9>(dig);
     int leader = __ffs(peers) - 1;
     uint32_t pos = 0;
     if (act) pos = wc[warp][dig] + __popc(peers & lt);
