@@ -58,10 +58,10 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "3d5ee3fc58c51697",
+    "source_sha256_16": "35377fa4740ccb04",
     "workload": "A2",
-    "raster_fwd": 262.734592e6 + 17.832704e6,
-    "raster_bwd": 421.471744e6 + 95.915264e6,
+    "raster_fwd": 261.407744e6 + 17.613056e6,
+    "raster_bwd": 419.449344e6 + 95.203328e6,
 }
 
 
