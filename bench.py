@@ -9,10 +9,11 @@ independent replica on its own GPU (its own batch): the method's images are
 independent, so the step shards with no data-path collective ("weak"
 scaling); value = images of all ranks / the slowest rank's time.
 
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
-on the library's stream with an L2 flush (a 256 MB write) between steps,
-outside the events; barrier + synchronize on both sides of the timed region;
-max over ranks.  The ``e2e`` figure repeats the step through the public API
+Timing: W untimed warm-up steps, the end-to-end loop, then K steps back to
+back, each bracketed by CUDA events on the library's stream with an L2 flush
+(a 256 MB write) between steps, outside the events; barrier + synchronize on
+both sides of the timed region; max over ranks.  The per-stage times come
+from a separate pass with the library's stage events on.  The ``e2e`` figure repeats the step through the public API
 with the step's inputs copied from pinned host memory and the loss and
 gradient copied back inside the timed region.
 """
@@ -100,7 +101,8 @@ def parse():
     ap.add_argument("--impl", choices=["gem", "reference"], default="gem")
     ap.add_argument("--workload", default="A2")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain dense form")
-    ap.add_argument("--no-query", action="store_true", help="skip timing the density query")
+    ap.add_argument("--no-query", action="store_true",
+                    help="skip timing the density query, FSC, training iteration and nearest neighbours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return ap.parse_args()
 
@@ -314,45 +316,45 @@ def main():
 
     warm = max(args.warmup, 3)
     for _ in range(warm):
+        flush.zero_()
         step()
     torch.cuda.synchronize()
     if ctx.gem_status() != 0:
         raise RuntimeError("device status after warm-up: " + ctx.lib.gem_last_error(ctx.h).decode())
 
-    # ---- device-timed region ------------------------------------------------
-    ctx.gem_timing(True)
-    stage_ms = {k: 0.0 for k in binding.STAGES}
-    launches = 0
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # the clock sampler runs from here to the end of the device-timed region
     clocks = ClockSampler(physical_gpu(local))
     clocks.start()
     time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        ms, ln = ctx.gem_timing_read()  # synchronises
-        for k in stage_ms:
-            stage_ms[k] += ms[k]
-        launches += sum(ln.values())
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ctx.gem_timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    status = ctx.gem_status()
-    if status != 0:
-        raise RuntimeError("device status after timed region: " + ctx.lib.gem_last_error(ctx.h).decode())
-    total_max = reduce_max(total_s, dev)
-    value = throughput(w.B * args.steps, total_max, ws)
 
-    # ---- end to end through the public API, host buffers ----------------------
+    # ---- plain dense form (timed before the tiled path; its load also
+    # brings the GPU to its clocks) ----------------------------------------------
+    plain = None
+    if not args.no_plain:
+        pd = torch.empty(w.B, w.d, w.d, device=dev)
+        dp = torch.empty(w.B, w.d, w.d, device=dev)
+        g2 = torch.empty(w.M, 11, device=dev)
+
+        def pstep():
+            ctx.gem_project_dense(D["params"], D["R"], D["t"], pd)
+            ctx.gem_ctf_loss(pd, D["images"], ctf_params=D["ctf_params"], dproj=dp, loss=loss)
+            ctx.gem_project_backward_dense(dp, g2)
+
+        pstep()
+        torch.cuda.synchronize()
+        n_plain = 2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_plain):
+            pstep()
+        b.record(stream)
+        torch.cuda.synchronize()
+        pv = w.B * n_plain / (a.elapsed_time(b) / 1e3)
+        plain = {"value": pv, "unit": UNIT,
+                 "form": "one thread per pixel over all M Gaussians; one thread per (image, Gaussian) over all pixels"}
+
+    # ---- end to end through the public API, host buffers (run before the
+    # device-timed region, whose steps follow it directly) ---------------------
     pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in ("images", "R", "t", "ctf_params")}
     out_grad = torch.empty(w.M, 11).pin_memory()
     out_loss = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -379,12 +381,55 @@ def main():
     e2e = {"value": throughput(w.B * e2e_steps, e2e_s, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
+    # ---- device-timed region: K steps back to back ----------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ctx.gem_status() != 0:
+        raise RuntimeError("device status after the end-to-end loop: " + ctx.lib.gem_last_error(ctx.h).decode())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    status = ctx.gem_status()
+    if status != 0:
+        raise RuntimeError("device status after timed region: " + ctx.lib.gem_last_error(ctx.h).decode())
+    total_max = reduce_max(total_s, dev)
+    value = throughput(w.B * args.steps, total_max, ws)
+    step_loss = float(loss.item())
+    if plain is not None:
+        plain["speedup_of_tiled"] = value / ws / plain["value"]
+
+    # ---- per-stage device times and launch counts: a separate pass with the
+    # library's stage events on (reading them synchronises after every step)
+    ctx.gem_timing(True)
+    n_stage = max(1, min(args.steps, 20))
+    stage_ms = {k: 0.0 for k in binding.STAGES}
+    launches_per_step = 0
+    for i in range(n_stage):
+        flush.zero_()
+        step()
+        ms, ln = ctx.gem_timing_read()
+        for k in stage_ms:
+            stage_ms[k] += ms[k]
+        launches_per_step = sum(ln.values())
+    ctx.gem_timing(False)
+    launches = launches_per_step * args.steps
+
     # ---- roofline of the dominant kernel ----------------------------------------
     kept, evaluated = ctx.gem_pair_stats()
     pairs = ctx.gem_pair_count()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    per_stage = {k: v / args.steps for k, v in stage_ms.items()}
+    per_stage = {k: v / n_stage for k, v in stage_ms.items()}
     dom = max(("raster_fwd", "raster_bwd"), key=lambda k: per_stage[k])
     mhz = clk.get("sm_mhz") or 1455.0
     ops = FP32_OPS_PER_KEPT_PAIR[dom]
@@ -408,31 +453,6 @@ def main():
                          "note": "one SFU exponential per kept pair, no other work counted"},
             "kept_pairs_per_launch": kept, "evaluated_pairs_per_launch": evaluated,
             "listed_pairs_per_launch": pairs}
-
-    # ---- plain dense form -------------------------------------------------------
-    plain = None
-    if not args.no_plain:
-        pd = torch.empty(w.B, w.d, w.d, device=dev)
-        dp = torch.empty(w.B, w.d, w.d, device=dev)
-        g2 = torch.empty(w.M, 11, device=dev)
-
-        def pstep():
-            ctx.gem_project_dense(D["params"], D["R"], D["t"], pd)
-            ctx.gem_ctf_loss(pd, D["images"], ctf_params=D["ctf_params"], dproj=dp, loss=loss)
-            ctx.gem_project_backward_dense(dp, g2)
-
-        pstep()
-        torch.cuda.synchronize()
-        n_plain = 2
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(n_plain):
-            pstep()
-        b.record(stream)
-        torch.cuda.synchronize()
-        pv = w.B * n_plain / (a.elapsed_time(b) / 1e3)
-        plain = {"value": pv, "unit": UNIT, "speedup_of_tiled": value / ws / pv,
-                 "form": "one thread per pixel over all M Gaussians; one thread per (image, Gaussian) over all pixels"}
 
     # ---- density query on the d^3 grid (Eq. query) -----------------------------
     query = None
@@ -490,6 +510,60 @@ def main():
                           "roofline": {"bound": "alu", "kernel": "whole query", "achieved": qa, "peak": qpeak,
                                        "unit": "Gpair/s", "frac": qa / qpeak}})
 
+    # ---- training iteration (step + Adam on raw parameters), nearest neighbours
+    train = None
+    if not args.no_query:
+        raw = D["params"].clone()
+        raw[:, 3:6] = torch.log(raw[:, 3:6].abs())
+        raw[:, 10] = torch.log(raw[:, 10])
+        m_a, v_a, p_a = torch.zeros_like(raw), torch.zeros_like(raw), torch.empty_like(raw)
+        ctx.gem_activate(raw, p_a)
+        lr = (1e-3, 1e-3, 1e-3, 1e-3)
+        nn_d = torch.empty(w.M, 1, device=dev)
+        nn_i = torch.empty(w.M, 1, dtype=torch.int32, device=dev)
+
+        def tstep(i):
+            ctx.gem_forward(p_a, D["R"], D["t"], D["images"], loss, ctf_params=D["ctf_params"])
+            ctx.gem_backward(grad)
+            ctx.gem_adam_step(raw, m_a, v_a, grad, p_a, lr, i + 1)
+
+        for i in range(3):
+            tstep(i)
+        torch.cuda.synchronize()
+        nt = 10
+        te = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nt)]
+        ae = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nt)]
+        ke = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nt)]
+        for i in range(nt):
+            flush.zero_()
+            te[i][0].record(stream)
+            tstep(3 + i)
+            te[i][1].record(stream)
+            flush.zero_()
+            ae[i][0].record(stream)
+            ctx.gem_adam_step(raw, m_a, v_a, grad, p_a, lr, 4 + nt + i)
+            ae[i][1].record(stream)
+            flush.zero_()
+            ke[i][0].record(stream)
+            ctx.gem_nn_distance(p_a, 1, nn_d, nn_i)
+            ke[i][1].record(stream)
+        torch.cuda.synchronize()
+        if ctx.gem_status() != 0:
+            raise RuntimeError("device status after the training loop: " + ctx.lib.gem_last_error(ctx.h).decode())
+        t_ms = sum(a.elapsed_time(b) for a, b in te) / nt
+        a_ms = sum(a.elapsed_time(b) for a, b in ae) / nt
+        k_ms = sum(a.elapsed_time(b) for a, b in ke) / nt
+        a_bytes = 8 * 4 * w.M * 11  # raw, m, v, grad read; raw, m, v, params written
+        a_gbs = a_bytes / (a_ms / 1e3) / 1e9
+        train = {"images_per_s": w.B / (t_ms / 1e3), "ms_per_iteration": t_ms,
+                 "iteration": "projection, CTF + loss + adjoint, sparse gradient, Adam on raw parameters",
+                 "adam_ms": a_ms,
+                 "adam_roofline": {"bound": "hbm", "achieved": a_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                   "frac": a_gbs / HBM_PEAK_GBS, "algorithmic_bytes": a_bytes,
+                                   "peak_note": HBM_PEAK_NOTE},
+                 "nearest_neighbour_ms": k_ms, "nearest_neighbour_k": 1,
+                 "l2": "flushed before each timed call (256 MB write)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w)
@@ -501,7 +575,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w), "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "plain": plain,
-            "stages_ms": per_stage, "loss": float(loss.item()), "query": query,
+            "stages_ms": per_stage, "loss": step_loss, "query": query, "train": train,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
