@@ -62,6 +62,7 @@ def _load():
                 "gem_oracle_ctf_apply": (None, [I, I, P, P, P]),
                 "gem_oracle_loss": (D, [I, I, P, P, P, P, P, P]),
                 "gem_oracle_grad": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
+                "gem_oracle_grad_abs": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
                 "gem_oracle_query": (None, [I, D, D, I, L, P, P]),
                 "gem_oracle_query_voxels": (None, [I, D, D, I, L, P, L, P, P]),
             }
@@ -196,9 +197,12 @@ def loss(hfull, proj, images):
 
 
 def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None, no_rotation=False,
-         isotropic=False) -> np.ndarray:
-    """dL/dtheta [nsel][11] given g = dL/dproj [B][d][d]."""
+         isotropic=False, absolute=False) -> np.ndarray:
+    """dL/dtheta [nsel][11] given g = dL/dproj [B][d][d].  absolute=True: the sum
+    of the absolute values of the per-pixel terms instead, the scale that
+    bounds the rounding error of a float32 sum of them (test infrastructure)."""
     if no_rotation or isotropic:
+        assert not absolute
         ge = grad(constrained(params, no_rotation, isotropic), R, t, d, apix, tau, g, norm_mode, sel)
         return fold_grad(ge, no_rotation, isotropic)
     params, R, t, g = _f64(params), _f64(R), _f64(t), _f64(g)
@@ -209,8 +213,8 @@ def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None, no_rotatio
         sel_arr = np.ascontiguousarray(np.asarray(sel, dtype=np.int64))
         nsel, selp = sel_arr.shape[0], _ptr(sel_arr)
     out = np.zeros((nsel, NPAR))
-    _load().gem_oracle_grad(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(g),
-                            nsel, selp, _ptr(out))
+    fn = _load().gem_oracle_grad_abs if absolute else _load().gem_oracle_grad
+    fn(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(g), nsel, selp, _ptr(out))
     return out
 
 

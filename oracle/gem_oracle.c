@@ -483,10 +483,30 @@ double gem_oracle_loss(int d, int B, const double *hfull, const double *proj,
 /* sel: indices of the Gaussians wanted (NULL: all M, then nsel = M).        */
 /* grad: [nsel][11].                                                         */
 /* ------------------------------------------------------------------------ */
+/* absolute != 0: the same loop summing |g * dvalue/dtheta| instead (the scale
+ * against which the rounding error of a float sum of these terms is bounded;
+ * test infrastructure, not part of the method). */
+static void grad_loop(int d, double apix, double tau, int norm_mode, const double *params, int B,
+                      const double *Rv, const double *tv, const double *g, int64_t nsel,
+                      const int64_t *sel, int absolute, double *grad);
+
 void gem_oracle_grad(int d, double apix, double tau, int norm_mode, int64_t M,
                      const double *params, int B, const double *Rv, const double *tv,
                      const double *g, int64_t nsel, const int64_t *sel, double *grad) {
   (void)M;
+  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 0, grad);
+}
+
+void gem_oracle_grad_abs(int d, double apix, double tau, int norm_mode, int64_t M,
+                         const double *params, int B, const double *Rv, const double *tv,
+                         const double *g, int64_t nsel, const int64_t *sel, double *grad) {
+  (void)M;
+  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 1, grad);
+}
+
+static void grad_loop(int d, double apix, double tau, int norm_mode, const double *params, int B,
+                      const double *Rv, const double *tv, const double *g, int64_t nsel,
+                      const int64_t *sel, int absolute, double *grad) {
   int64_t n = (int64_t)d * d;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < nsel; ++i) {
@@ -509,7 +529,7 @@ void gem_oracle_grad(int d, double apix, double tau, int norm_mode, int64_t M,
             double t = pg.dlnamp[m] + w0 * pg.dmean[0][m] + w1 * pg.dmean[1][m] +
                        0.5 * (w0 * (pg.dcov[0][0][m] * w0 + pg.dcov[0][1][m] * w1) +
                               w1 * (pg.dcov[1][0][m] * w0 + pg.dcov[1][1][m] * w1));
-            acc[m] += gv * t;
+            acc[m] += absolute ? fabs(gv * t) : gv * t;
           }
         }
     }

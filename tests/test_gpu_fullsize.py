@@ -12,7 +12,7 @@ from paper_2509_25075_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
-FULL = ["A2", "A3", "A5"]
+FULL = ["A2", "A3", "A4", "A5"]
 
 
 def _ctx(w):
@@ -88,12 +88,22 @@ def test_fullsize_gradient_sampled_gaussians(name):
     rng = np.random.default_rng(101)
     sel = rng.choice(w.M, size=12, replace=False)
     ref = oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g, sel=sel)
+    # the scale of the rounding error of float32 sums of the per-pixel terms
+    absum = oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g, sel=sel,
+                        absolute=True)
     got = grad.cpu().numpy()[sel].astype(np.float64)
-    # per sampled Gaussian: relative error of its 11-vector
+    u = 2.0 ** -24
+    # per entry: a float32 sum of terms whose absolute sum is A carries an
+    # error up to gamma_n A, gamma_n ~ n u for chains of n additions; the
+    # longest chain here is ~80 (a lane's rows and blocks, then one atomic add
+    # per tile of a 12-px Gaussian), and the moments' separate sums exceed A
+    # by up to ~3 where the terms of a pixel cancel: 256 u A, plus 1e-5 of the
+    # entry's Gaussian
     for k in range(len(sel)):
         nrm = np.linalg.norm(ref[k])
         if nrm == 0:
             assert np.all(got[k] == 0)
             continue
-        assert np.linalg.norm(got[k] - ref[k]) <= 1e-4 * nrm, (sel[k], got[k], ref[k])
+        bound = 1e-5 * nrm + 256 * u * absum[k]
+        assert np.all(np.abs(got[k] - ref[k]) <= bound), (sel[k], got[k], ref[k], absum[k])
     ctx.close()

@@ -404,6 +404,23 @@ def test_rho_gradient_is_linear(norm_mode):
         assert G[j, 10] == pytest.approx(np.sum(g * img_j) / th[j, 10], rel=1e-12, abs=1e-18)
 
 
+def test_absolute_gradient_terms():
+    """The absolute sums (the error scale of a float32 gradient) bound the
+    gradient, and for rho, whose per-pixel terms are g * value / rho, equal
+    <|g|, image_j> / rho_j exactly."""
+    th, Rv, t, imgs, H, d, apix = _case(25, M=4)
+    tau = 2e-3
+    proj = oracle.project(th, Rv, t, d, apix, tau)
+    _, _, _, g = oracle.loss(H, proj, imgs)
+    G = oracle.grad(th, Rv, t, d, apix, tau, g)
+    A = oracle.grad(th, Rv, t, d, apix, tau, g, absolute=True)
+    assert np.all(A >= np.abs(G) * (1 - 1e-12))
+    assert np.any(A > 2 * np.abs(G))  # the smooth-field terms do cancel
+    for j in range(4):
+        img_j = oracle.project(th[j:j + 1], Rv, t, d, apix, tau)
+        assert A[j, 10] == pytest.approx(np.sum(np.abs(g) * img_j) / th[j, 10], rel=1e-12, abs=1e-18)
+
+
 def test_gradient_selection_matches_full():
     th, Rv, t, imgs, H, d, apix = _case(24, M=5)
     proj = oracle.project(th, Rv, t, d, apix, 1e-3)
