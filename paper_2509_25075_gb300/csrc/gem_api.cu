@@ -30,6 +30,7 @@ struct gem_ctx {
 
   BinScratch bin{};
   float *mom = nullptr;
+  bool mom_clean = false;  // every moment is zero (prep_bwd leaves them so)
   float *part = nullptr;
   int nbg = 1;
   float *proj = nullptr;   // internal projection of gem_forward
@@ -396,11 +397,13 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     return fail(c, GEM_ESTATE, "the last projection was dense: no tile lists to differentiate");
   const gem_config &g = c->cfg;
   cudaError_t e;
-  size_t mbytes = (size_t)c->B * c->M * 6 * sizeof(float);
+  // the whole buffer, should an earlier pass have stopped before clearing it
+  size_t mbytes = (size_t)g.max_B * g.max_M * 6 * sizeof(float);
   {
     StageScope sc(c, GEM_STAGE_RASTER_BWD, 1);
-    if (!dense && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
+    if (!dense && !c->mom_clean && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "moment clear");
+    c->mom_clean = false;
     if (dense)
       e = launch_dense_bwd(c->rec, c->M, c->B, g.d, c->l2tau, dproj, c->mom, c->stream);
     else
@@ -412,6 +415,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
   if ((e = launch_prep_bwd(c->params, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode, shape_flags(g),
                            c->mom, c->part, c->nbg, grad, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "prep_bwd");
+  c->mom_clean = true;
   return GEM_OK;
 }
 

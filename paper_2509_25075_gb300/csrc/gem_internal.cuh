@@ -256,9 +256,11 @@ cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, int
 cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
                              const float *t, float apix, int d, float l2tau, float zrange,
                              Rec *rec, uint16_t *key, cudaStream_t st);
+// Reads the moments [B][M][6] and leaves them zero (the next backward pass
+// accumulates into them).
 cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
                             const float *R, const float *t, float apix, int d, int norm_mode,
-                            int shape, const float *mom, float *part, int nbg, float *grad,
+                            int shape, float *mom, float *part, int nbg, float *grad,
                             cudaStream_t st);
 cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t M, int B,
                                    const float *R, const float *t, float apix, int d, float *out,

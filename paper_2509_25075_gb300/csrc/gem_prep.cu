@@ -194,7 +194,7 @@ struct Kahan {
 __global__ void __launch_bounds__(128) prep_bwd_kernel(
     const float *__restrict__ params, const GaussPrep *__restrict__ gp, int64_t M, int B,
     const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode, int shape,
-    const float *__restrict__ mom, int per_group, float *__restrict__ part) {
+    float *__restrict__ mom, int per_group, float *__restrict__ part) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int bg = blockIdx.y;
   if (j >= M) return;
@@ -209,9 +209,12 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   float inv = 1.f / apix;
   int b0 = bg * per_group, b1 = min(B, b0 + per_group);
   for (int b = b0; b < b1; ++b) {
-    const float *mm = mom + ((int64_t)b * M + j) * 6;
-    float m0 = mm[0], m1 = mm[1], m2 = mm[2], m3 = mm[3], m4 = mm[4], m5 = mm[5];
+    float2 *mm = reinterpret_cast<float2 *>(mom + ((int64_t)b * M + j) * 6);
+    const float2 ma = mm[0], mb = mm[1], mc = mm[2];
+    float m0 = ma.x, m1 = ma.y, m2 = mb.x, m3 = mb.y, m4 = mc.x, m5 = mc.y;
     if (m0 == 0.f && m1 == 0.f && m2 == 0.f && m3 == 0.f && m4 == 0.f && m5 == 0.f) continue;
+    // leave the moments cleared for the next backward pass
+    mm[0] = mm[1] = mm[2] = make_float2(0.f, 0.f);
     float Rl[9], tl[2];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__
 
 cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
                             const float *R, const float *t, float apix, int d, int norm_mode,
-                            int shape, const float *mom, float *part, int nbg, float *grad,
+                            int shape, float *mom, float *part, int nbg, float *grad,
                             cudaStream_t st) {
   int per = (B + nbg - 1) / nbg;
   int groups = (B + per - 1) / per;
