@@ -61,8 +61,8 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 CAPTURED_TRAFFIC = {
     "source_sha256_16": "35377fa4740ccb04",
     "workload": "A2",
-    "raster_fwd": 261.407744e6 + 17.613056e6,
-    "raster_bwd": 419.449344e6 + 95.203328e6,
+    "raster_fwd": 261.132288e6 + 18.030336e6,
+    "raster_bwd": 419.187968e6 + 94.786560e6,
 }
 
 
