@@ -13,7 +13,7 @@
 // input order.  The result is deterministic: no position depends on thread
 // timing.  Each list entry also gets the mask of the 4x4 pixel blocks of
 // its tile that the Gaussian's region above tau meets.  The tile count pass
-// does all the geometry (candidate tiles, exact tile tests, block masks) and
+// does all the geometry (candidate tiles, block-row ranges, block masks) and
 // records each hit; the scatter pass only ranks and writes them.
 #include "gem_internal.cuh"
 
@@ -162,37 +162,100 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
 
 // ------------------------------------------------------ tile binning ----
 
-// The tiles a record may touch: the pixel rectangle of its extent, cut to
-// the image, then each tile tested exactly against the ellipse.
-struct TileRect {
-  int tx0, tx1, ty0, ty1;
+// Geometry of the region e > log2(tau) - margin of one record, in pixel
+// units: Q(dx, dy) = al dx^2 + be dx dy + ga dy^2 <= kap with al = -ca,
+// be = -cb, ga = -cc and kap = l2A - log2(tau) + margin, reduced to what the
+// block-row ranges need (computed once per record).  Row dy of the region
+// spans dx in [c(dy) - h(dy), c(dy) + h(dy)] with
+//   c(dy) = -be dy / (2 al),  h(dy) = sqrt(4 al kap - D dy^2) / (2 al),
+//   D = 4 al ga - be^2;
+// the region's y-extent is +-sqrt(4 al kap / D), its x-extent
+// +-sqrt(4 ga kap / D), reached at dy = dyL = be xext / (2 ga) (left) and
+// -dyL (right).
+struct RowGeo {
+  float px, py;  // centre
+  float k4a, D;  // 4 al kap (infinite when tau = 0), 4 al ga - be^2
+  float i2a, sl; // 1 / (2 al), -be / (2 al)
+  float dyL;
+  float xext, yext;
 };
 
-__device__ __forceinline__ bool rec_tiles(const Rec &r, int d, TileRect &tr) {
-  int ulo, uhi, vlo, vhi;
-  if (!pixel_range(r.a.x, r.b.z, d, ulo, uhi)) return false;
-  if (!pixel_range(r.a.y, r.b.w, d, vlo, vhi)) return false;
-  tr.tx0 = ulo / kTile;
-  tr.tx1 = uhi / kTile;
-  tr.ty0 = vlo / kTile;
-  tr.ty1 = vhi / kTile;
-  return true;
+// The approximate square roots and divisions (a few ulp) are absorbed by the
+// margin already in kap, so the ranges stay supersets of the exact ones.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  x = fmaxf(x, 0.f);
+  return x * rsqrtf(fmaxf(x, 1e-30f));
+}
+
+__device__ __forceinline__ RowGeo make_row_geo(const Rec &r, float l2tau) {
+  const float al = -r.a.z, be = -r.a.w, ga = -r.b.x;
+  const float kap = r.b.y - l2tau + kMargin;
+  RowGeo G;
+  G.px = r.a.x;
+  G.py = r.a.y;
+  G.i2a = __fdividef(0.5f, al);
+  G.sl = -be * G.i2a;
+  G.D = 4.f * al * ga - be * be;
+  G.k4a = 4.f * al * kap;
+  const float iD = __fdividef(1.f, G.D);
+  G.xext = sqrt_approx(4.f * ga * kap * iD);
+  G.yext = sqrt_approx(G.k4a * iD);
+  G.dyL = be * G.xext * __fdividef(0.5f, ga);
+  return G;
+}
+
+// Block columns (4-pixel columns of the whole image, 0 .. nb-1) that the
+// region meets in block row by (pixel rows 4 by .. 4 by + 3), packed as
+// lo | hi << 8, or kNoRow.  Inside the strip the region's x-range is
+// [c - h, c + h] at the strip's two ends, widened to the region's own
+// x-extreme where the strip contains the row that reaches it.  Every
+// rounding step is explicit (no contraction the compiler could choose per
+// call site), so each inlined copy returns the same bits for the same input.
+constexpr unsigned kNoRow = 0x00ffu;  // lo = 255 > hi = 0
+__device__ __forceinline__ float sqrt_rn_approx(float x) {
+  x = fmaxf(x, 0.f);
+  return __fmul_rn(x, rsqrtf(fmaxf(x, 1e-30f)));
+}
+__device__ __forceinline__ unsigned block_row_range(const RowGeo &G, int by, int nb) {
+  if (!(G.k4a < INFINITY)) return (unsigned)(nb - 1) << 8;  // tau = 0: every pixel counts
+  float a = __fsub_rn((float)(4 * by), G.py), b = __fadd_rn(a, 3.f);
+  a = fmaxf(a, -G.yext);
+  b = fminf(b, G.yext);
+  if (!(a <= b)) return kNoRow;
+  const float ha = __fmul_rn(sqrt_rn_approx(__fmaf_rn(__fmul_rn(-G.D, a), a, G.k4a)), G.i2a);
+  const float hb = __fmul_rn(sqrt_rn_approx(__fmaf_rn(__fmul_rn(-G.D, b), b, G.k4a)), G.i2a);
+  const float ca = __fmul_rn(G.sl, a), cb = __fmul_rn(G.sl, b);
+  float xmin = fminf(__fsub_rn(ca, ha), __fsub_rn(cb, hb));
+  float xmax = fmaxf(__fadd_rn(ca, ha), __fadd_rn(cb, hb));
+  if (G.dyL >= a && G.dyL <= b) xmin = -G.xext;
+  if (-G.dyL >= a && -G.dyL <= b) xmax = G.xext;
+  // columns bx whose pixel centres [4 bx, 4 bx + 3] meet [px + xmin, px + xmax]
+  const float lo = fmaxf(ceilf(__fmul_rn(__fsub_rn(__fadd_rn(G.px, xmin), 3.f), 0.25f)), 0.f);
+  const float hi = fminf(floorf(__fmul_rn(__fadd_rn(G.px, xmax), 0.25f)), (float)(nb - 1));
+  if (!(lo <= hi)) return kNoRow;
+  return (unsigned)lo | ((unsigned)hi << 8);
 }
 
 // Shared staging of one chunk of 256 Gaussians (depth order): each
-// Gaussian's record and candidate tile rectangle, and the exclusive prefix
-// of the candidate counts, so that the chunk's (Gaussian, candidate tile)
-// pairs can be spread evenly over the threads whatever the Gaussians' sizes.
-constexpr int kOwnerCap = 8192;  // candidates per chunk with a byte owner map
+// Gaussian's row geometry, candidate tile rectangle (the tiles its extent
+// box meets) and block-row range, with exclusive prefixes of the candidate
+// and block-row counts, so that the chunk's (Gaussian, block row) and
+// (Gaussian, candidate tile) items can be spread evenly over the threads
+// whatever the Gaussians' sizes.  Each block row's column range is computed
+// once and shared by every candidate tile of the Gaussian in that row.
+constexpr int kOwnerCap = 4096;  // candidates per chunk with a byte owner map
+constexpr int kRowCap = 2048;    // block rows per chunk whose ranges are staged
 
 struct ChunkStage {
-  Ell ell[kChunkT];
-  uint32_t j[kChunkT];
-  int rect[kChunkT];      // tx0 | ty0 << 8 | width << 16 (0 width: no tile)
-  float inv_w[kChunkT];   // 1 / width, to split a candidate index into rows
-  int off[kChunkT + 1];   // exclusive prefix of candidate counts; off[kChunkT] = total
-  int wsum[kChunkT / 32];
-  unsigned char owner[kOwnerCap];  // owner slot of each candidate (when they fit)
+  RowGeo geo[kChunkT];
+  unsigned rect[kChunkT];  // tx0 | ty0 << 8 | width << 16 | first block row << 24
+  float inv_w[kChunkT];    // 1 / width, to split a candidate index into rows
+  int off[kChunkT + 1];    // exclusive prefix of candidate counts; off[kChunkT] = total
+  int roff[kChunkT + 1];   // exclusive prefix of block-row counts; roff[kChunkT] = rows
+  int wsum[kChunkT / 32], wrow[kChunkT / 32];
+  unsigned char owner[kOwnerCap];   // owner slot of each candidate (when they fit)
+  unsigned char rowner[kRowCap];    // owner slot of each block row (when they fit)
+  unsigned short rowx[kRowCap];     // block-row column ranges (when they fit)
 };
 
 __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict__ rec,
@@ -200,40 +263,59 @@ __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict
                                             int b, int c, int d, float l2tau) {
   const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
   const int64_t r = (int64_t)c * kChunkT + i;
-  int ncand = 0, packed = 0;
+  int ncand = 0, nrow = 0;
+  unsigned packed = 0;
   if (r < M) {
     const uint32_t j = perm ? perm[(int64_t)b * M + r] : (uint32_t)r;
     const Rec rc = rec[(int64_t)b * M + j];
-    S.ell[i] = make_ell(rc, l2tau);
-    S.j[i] = j;
-    TileRect tr;
-    if (rec_tiles(rc, d, tr)) {
-      const int w = tr.tx1 - tr.tx0 + 1;
-      ncand = w * (tr.ty1 - tr.ty0 + 1);
-      packed = tr.tx0 | (tr.ty0 << 8) | (w << 16);
+    S.geo[i] = make_row_geo(rc, l2tau);
+    int ulo, uhi, vlo, vhi;
+    if (pixel_range(rc.a.x, rc.b.z, d, ulo, uhi) && pixel_range(rc.a.y, rc.b.w, d, vlo, vhi)) {
+      const int tx0 = ulo / kTile, ty0 = vlo / kTile;
+      const int w = uhi / kTile - tx0 + 1;
+      ncand = w * (vhi / kTile - ty0 + 1);
+      nrow = (vhi >> 2) - (vlo >> 2) + 1;
+      packed = (unsigned)tx0 | ((unsigned)ty0 << 8) | ((unsigned)w << 16) |
+               ((unsigned)(vlo >> 2) << 24);
       S.inv_w[i] = 1.f / (float)w;
     }
   }
   S.rect[i] = packed;
-  int inc = ncand;
+  // both counts in one scan: a warp's candidates fit 17 bits (32 x 48 x 48),
+  // its block rows 13 (32 x 192)
+  int inc = ncand | (nrow << 17);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     int v = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += v;
   }
-  if (lane == 31) S.wsum[warp] = inc;
+  const int incc = inc & 0x1ffff, incr = inc >> 17;
+  if (lane == 31) {
+    S.wsum[warp] = incc;
+    S.wrow[warp] = incr;
+  }
   __syncthreads();
-  int base = 0, total = 0;
+  int base = 0, total = 0, rbase = 0, rows = 0;
 #pragma unroll
   for (int w = 0; w < kChunkT / 32; ++w) {
-    if (w < warp) base += S.wsum[w];
+    if (w < warp) {
+      base += S.wsum[w];
+      rbase += S.wrow[w];
+    }
     total += S.wsum[w];
+    rows += S.wrow[w];
   }
-  const int my = base + inc - ncand;
+  const int my = base + incc - ncand, myr = rbase + incr - nrow;
   S.off[i] = my;
-  if (i == 0) S.off[kChunkT] = total;
+  S.roff[i] = myr;
+  if (i == 0) {
+    S.off[kChunkT] = total;
+    S.roff[kChunkT] = rows;
+  }
   if (total <= kOwnerCap)
     for (int q = 0; q < ncand; ++q) S.owner[my + q] = (unsigned char)i;
+  if (rows <= kRowCap)
+    for (int q = 0; q < nrow; ++q) S.rowner[myr + q] = (unsigned char)i;
   __syncthreads();
 }
 
@@ -242,11 +324,11 @@ __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict
 // away from an integer and its floor is the exact row.
 __device__ __forceinline__ void candidate_tile(const ChunkStage &S, int o, int q, int &tx,
                                                int &ty) {
-  const int pr = S.rect[o];
-  const int w = (pr >> 16) & 0xffff;
+  const unsigned pr = S.rect[o];
+  const int w = (int)((pr >> 16) & 0xffu);
   const int row = (int)(((float)q + 0.5f) * S.inv_w[o]);
-  tx = (pr & 0xff) + (q - row * w);
-  ty = ((pr >> 8) & 0xff) + row;
+  tx = (int)(pr & 0xffu) + (q - row * w);
+  ty = (int)((pr >> 8) & 0xffu) + row;
 }
 
 // Owner (Gaussian slot) of candidate k: from the byte map when the chunk's
@@ -262,48 +344,70 @@ __device__ __forceinline__ int candidate_owner(const ChunkStage &S, int k, int t
   return lo;
 }
 
+// 4x4-block mask of candidate tile (tx, ty) of slot o: bit 4 lb + bx set when
+// the Gaussian's range in block row 4 ty + lb covers block column 4 tx + bx.
+// The rows come from the staging, or, when the chunk's rows did not fit it,
+// from block_row_range directly; either way the count and the write pass of
+// a candidate get the same bits.
+__device__ __forceinline__ unsigned candidate_mask(const ChunkStage &S, bool staged, int o,
+                                                   int tx, int ty, int nb) {
+  const int by0 = (int)(S.rect[o] >> 24), r0 = S.roff[o], nr = S.roff[o + 1] - r0;
+  const int bx0 = 4 * tx;
+  unsigned m = 0;
+#pragma unroll
+  for (int lb = 0; lb < 4; ++lb) {
+    const int rr = 4 * ty + lb - by0;
+    if (rr < 0 || rr >= nr) continue;
+    const unsigned v = staged ? (unsigned)S.rowx[r0 + rr] : block_row_range(S.geo[o], by0 + rr, nb);
+    const int l = max((int)(v & 255u), bx0), h = min((int)(v >> 8), bx0 + 3);
+    if (l <= h) m |= ((1u << (h - l + 1)) - 1u) << (4 * lb + l - bx0);
+  }
+  return m;
+}
+
 // Per chunk of 256 Gaussians (depth order) of image b: how many hit each
 // tile, written transposed, tcnt[b][t][c], so that each tile's column is
 // contiguous for the scan; and every hit, (slot o in the chunk, tile, 4x4-block
 // mask), in a run of hits[] claimed from a shared cursor, so that the scatter
-// pass repeats none of the geometry.  The run's contents and layout (threads
-// in order, each thread's candidates in order) do not depend on timing; only
+// pass repeats none of the geometry.  A candidate tile is a hit when its
+// block mask is not empty.  The run's contents and layout (threads in
+// order, each thread's candidates in order) do not depend on timing; only
 // where it starts does.
 __device__ __forceinline__ uint64_t pack_hit(int o, int t, unsigned mask) {
   return (uint64_t)o | ((uint64_t)t << 8) | ((uint64_t)mask << 24);
 }
 
-__global__ void __launch_bounds__(kChunkT) tile_count_kernel(
+__global__ void __launch_bounds__(kChunkT, 8) tile_count_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ perm, int64_t M, int d,
     float l2tau, int nch, uint32_t *__restrict__ tcnt, BinScratch bs) {
   extern __shared__ uint32_t tc[];
   __shared__ ChunkStage S;
-  __shared__ uint32_t hbits[kOwnerCap / 32];  // hit flag of each candidate (when they fit)
   __shared__ int wh[kChunkT / 32];
   __shared__ int64_t run_base;
   const int c = blockIdx.x, b = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nt = d / kTile, T = nt * nt;
+  const int nt = d / kTile, T = nt * nt, nb = d / 4;
   for (int i = threadIdx.x; i < T; i += blockDim.x) tc[i] = 0;
   stage_chunk(S, rec, perm, M, b, c, d, l2tau);
-  const int total = S.off[kChunkT];
-  const bool keep_bits = total <= kOwnerCap;
-  int nh = 0;
-  for (int k0 = 0; k0 < total; k0 += kChunkT) {
-    const int k = k0 + threadIdx.x;
-    bool hit = false;
-    if (k < total) {
-      const int o = candidate_owner(S, k, total);
-      int tx, ty;
-      candidate_tile(S, o, k - S.off[o], tx, ty);
-      hit = tile_hit(S.ell[o], tx * kTile, ty * kTile);
-      if (hit) {
-        atomicAdd(&tc[ty * nt + tx], 1u);
-        ++nh;
-      }
+  const int total = S.off[kChunkT], rows = S.roff[kChunkT];
+  const bool staged = rows <= kRowCap;
+  if (staged) {
+    // (Gaussian, block row) items spread over the threads
+    for (int q = threadIdx.x; q < rows; q += kChunkT) {
+      const int o = S.rowner[q];
+      S.rowx[q] = (unsigned short)block_row_range(S.geo[o], (int)(S.rect[o] >> 24) + q - S.roff[o], nb);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, hit);
-    if (keep_bits && lane == 0 && k0 + warp * 32 < total) hbits[(k0 >> 5) + warp] = bal;
+    __syncthreads();
+  }
+  int nh = 0;
+  for (int k = threadIdx.x; k < total; k += kChunkT) {
+    const int o = candidate_owner(S, k, total);
+    int tx, ty;
+    candidate_tile(S, o, k - S.off[o], tx, ty);
+    if (candidate_mask(S, staged, o, tx, ty, nb)) {
+      atomicAdd(&tc[ty * nt + tx], 1u);
+      ++nh;
+    }
   }
   // this thread's hits go after those of lower threads
   int inc = nh;
@@ -327,18 +431,15 @@ __global__ void __launch_bounds__(kChunkT) tile_count_kernel(
     bs.chunk_n[(int64_t)b * nch + c] = (uint32_t)H;
   }
   __syncthreads();
+  // the same candidates again, in the same order, with the same masks
   int64_t dst = run_base + before;
-  for (int k0 = 0; k0 < total && nh > 0; k0 += kChunkT) {
-    const int k = k0 + threadIdx.x;
-    if (k >= total) break;
+  for (int k = threadIdx.x; k < total && nh > 0; k += kChunkT) {
     const int o = candidate_owner(S, k, total);
     int tx, ty;
     candidate_tile(S, o, k - S.off[o], tx, ty);
-    const bool hit = keep_bits ? ((hbits[k >> 5] >> (k & 31)) & 1u) != 0
-                               : tile_hit(S.ell[o], tx * kTile, ty * kTile);
-    if (!hit) continue;
-    if (dst < bs.cap)
-      bs.hits[dst] = pack_hit(o, ty * nt + tx, block_mask16(S.ell[o], tx * kTile, ty * kTile));
+    const unsigned m = candidate_mask(S, staged, o, tx, ty, nb);
+    if (!m) continue;
+    if (dst < bs.cap) bs.hits[dst] = pack_hit(o, ty * nt + tx, m);
     ++dst;
     --nh;
   }

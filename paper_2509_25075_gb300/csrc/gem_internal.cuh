@@ -139,110 +139,6 @@ __device__ __forceinline__ bool pixel_range(float c, float r, int d, int &lo, in
   return true;
 }
 
-// Geometry of the region e > log2(tau) - margin of one record, in pixel
-// units: Q(dx, dy) = al dx^2 + be dx dy + ga dy^2 < kap with
-// kap = l2A - log2(tau) + margin, plus the constants the tile and block
-// tests need, computed once per record.
-struct Ell {
-  float px, py;        // centre
-  float al, be, ga;    // quadratic form (positive definite)
-  float kap;           // threshold of Q
-  float rx, ry;        // half extents of the region
-  float i2a, i2g;      // 1 / (2 al), 1 / (2 ga)
-  float D, k4a;        // 4 al ga - be^2, 4 al kap
-  float dyL;           // dy of the region's leftmost point (rightmost: -dyL)
-};
-
-// The approximate square roots and divisions (a few ulp) are absorbed by the
-// margin already in kap, so the tests stay supersets of the exact ones.
-__device__ __forceinline__ float sqrt_approx(float x) {
-  x = fmaxf(x, 0.f);
-  return x * rsqrtf(fmaxf(x, 1e-30f));
-}
-
-__device__ __forceinline__ Ell make_ell(const Rec &r, float l2tau) {
-  Ell E;
-  E.px = r.a.x;
-  E.py = r.a.y;
-  E.al = -r.a.z;
-  E.be = -r.a.w;
-  E.ga = -r.b.x;
-  E.kap = r.b.y - l2tau + kMargin;
-  E.rx = r.b.z;
-  E.ry = r.b.w;
-  E.i2a = __fdividef(0.5f, E.al);
-  E.i2g = __fdividef(0.5f, E.ga);
-  E.D = 4.f * E.al * E.ga - E.be * E.be;
-  E.k4a = 4.f * E.al * E.kap;
-  const float xext = sqrt_approx(4.f * E.ga * E.kap * __fdividef(1.f, E.D));
-  E.dyL = E.be * xext * E.i2g;
-  return E;
-}
-
-// Does the region meet the rectangle [x0, x0+side-1] x [y0, y0+side-1] of
-// pixel centres?  Exact minimum of Q over the rectangle compared with kap
-// (on an edge, the minimum of a 1D quadratic, clamped).
-__device__ __forceinline__ bool rect_hit(const Ell &E, int x0, int y0, int side) {
-  const float ax = (float)x0 - E.px, bx = ax + (float)(side - 1);
-  const float ay = (float)y0 - E.py, by = ay + (float)(side - 1);
-  if (ax > E.rx || bx < -E.rx || ay > E.ry || by < -E.ry) return false;
-  if (ax <= 0.f && bx >= 0.f && ay <= 0.f && by >= 0.f) return true;
-  float best = INFINITY;
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float dx = e ? bx : ax;
-    const float dy = fminf(fmaxf(-E.be * dx * E.i2g, ay), by);
-    best = fminf(best, E.al * dx * dx + E.be * dx * dy + E.ga * dy * dy);
-  }
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float dy = e ? by : ay;
-    const float dx = fminf(fmaxf(-E.be * dy * E.i2a, ax), bx);
-    best = fminf(best, E.al * dx * dx + E.be * dx * dy + E.ga * dy * dy);
-  }
-  return best <= E.kap;
-}
-
-__device__ __forceinline__ bool tile_hit(const Ell &E, int x0, int y0) {
-  return rect_hit(E, x0, y0, kTile);
-}
-
-// Bit 4 by + bx set when the region meets the pixel-centre rectangle of 4x4
-// block (bx, by) of the 16x16 tile whose top-left pixel is (x0, y0).  Row by
-// of blocks is a strip of dy; inside a strip the region's x-range is
-// [c - h, c + h] at the strip's ends, or the region's own x-extreme when
-// the strip contains the point where it is reached:
-//   c(dy) = -be dy / (2 al),  h(dy) = sqrt(4 al kap - D dy^2) / (2 al),
-//   x-extremes at dy = dyL (left) and -dyL (right), y-extent
-//   +-sqrt(4 al kap / D).
-__device__ __forceinline__ unsigned block_mask16(const Ell &E, int x0, int y0) {
-  if (!(E.kap < INFINITY)) return 0xffffu;  // tau = 0: every pixel counts
-  const float px = E.px - (float)x0, py = E.py - (float)y0;
-  const float yext = sqrt_approx(E.k4a * __fdividef(1.f, E.D));
-  const float xext = sqrt_approx(4.f * E.ga * E.kap * __fdividef(1.f, E.D));
-  unsigned m = 0;
-#pragma unroll
-  for (int by = 0; by < 4; ++by) {
-    float a = (float)(4 * by) - py, b = a + 3.f;
-    a = fmaxf(a, -yext);
-    b = fminf(b, yext);
-    if (!(a <= b)) continue;
-    const float ha = sqrt_approx(E.k4a - E.D * a * a) * E.i2a;
-    const float hb = sqrt_approx(E.k4a - E.D * b * b) * E.i2a;
-    const float ca = -E.be * a * E.i2a, cb = -E.be * b * E.i2a;
-    float xmin = fminf(ca - ha, cb - hb), xmax = fmaxf(ca + ha, cb + hb);
-    if (E.dyL >= a && E.dyL <= b) xmin = -xext;
-    if (-E.dyL >= a && -E.dyL <= b) xmax = xext;
-    // blocks bx whose centres [4 bx, 4 bx + 3] meet [px + xmin, px + xmax]
-    const float lo = fmaxf(ceilf((px + xmin - 3.f) * 0.25f), 0.f);
-    const float hi = fminf(floorf((px + xmax) * 0.25f), 3.f);
-    if (!(lo <= hi)) continue;
-    const int l = (int)lo, h = (int)hi;
-    m |= ((1u << (h - l + 1)) - 1u) << (4 * by + l);
-  }
-  return m;
-}
-
 // ---- launchers (each returns cudaError_t of the launch) ------------------
 
 // gem_prep.cu

@@ -19,9 +19,22 @@ SMALL = [
     syn.Workload("s64", d=64, M=733, B=3, apix=1.3, seed=12),
     syn.Workload("s32w", d=32, M=301, B=2, apix=1.0, s_lo=0.3, s_hi=6.0, n_clusters=4, seed=13),
 ]
+# Gaussians so large that the first chunk of 256 (depth order) has more block
+# rows than the tile count stages (big96: about 3100 of 2048), and also more
+# candidate tiles than its byte owner map holds (big128: about 5100 of
+# 4096), while the second chunk fits both: both paths run in one binning.
+# Their lists need more than the default 16 entries per (image, Gaussian)
+# (big128: about 17), so their contexts get 64.
+LARGE = [
+    syn.Workload("big96", d=96, M=300, B=2, apix=1.2, s_lo=3.0, s_hi=10.0, n_clusters=3, seed=14),
+    syn.Workload("big128", d=128, M=300, B=2, apix=1.2, s_lo=4.0, s_hi=12.0, n_clusters=3, seed=14),
+]
+LARGE_PAIRS = {w.name: 64 * w.B * w.M for w in LARGE}
 
 
 def _project(w, inp, dense=False, **kw):
+    if w.name in LARGE_PAIRS:
+        kw.setdefault("max_pairs", LARGE_PAIRS[w.name])
     ctx = gt.context(w, **kw)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
     args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
@@ -56,7 +69,7 @@ def test_records_match_oracle(w):
 
 
 @pytest.mark.parametrize("zsort", [1, 0])
-@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+@pytest.mark.parametrize("w", SMALL + LARGE, ids=lambda w: w.name)
 def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
     """Each tile list holds every Gaussian with a pixel above tau in that tile
     (brute force), only Gaussians whose extent box meets the tile, no
@@ -99,7 +112,7 @@ def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
                 assert np.all(np.diff(ent.astype(np.int64)) > 0)
 
 
-@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+@pytest.mark.parametrize("w", SMALL + LARGE, ids=lambda w: w.name)
 def test_kept_pair_count_matches_brute_force(w):
     """The rasteriser's walk (tile lists + 4x4 block masks) finds every pair
     whose value exceeds tau: its kept count equals the oracle's brute-force
@@ -135,6 +148,31 @@ def test_projection_matches_oracle(w, dense, norm_mode):
     ref = oracle.project(inp["params"], inp["R"], inp["t"], w.d, w.apix, tau, norm_mode)
     border = gt.borderline_pairs(inp, w, tau, norm_mode)
     gt.assert_proj_close(proj.cpu().numpy(), ref, tau, border)
+
+
+@pytest.mark.parametrize("w", LARGE, ids=lambda w: w.name)
+def test_large_gaussians_projection_and_gradient(w):
+    """Projection and gradient when the binning's chunk staging overflows.
+    A wide Gaussian's gradient entries are sums of thousands of per-pixel
+    terms of both signs (their absolute sum A reaches 4000 times the entry),
+    so each entry is held to the rounding bound of float32 sums used at full
+    size, 1e-5 of its Gaussian's gradient plus 256 u A, and the whole to the
+    usual norm tolerance."""
+    inp = gt.inputs(w)
+    ctx, _, proj = _project(w, inp)
+    ref = oracle.project(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau)
+    gt.assert_proj_close(proj.cpu().numpy(), ref, w.tau, gt.borderline_pairs(inp, w, w.tau))
+    g = syn.smooth_field(w) * 1e-3
+    grad = torch.empty(w.M, 11, device=gt.DEV)
+    ctx.gem_project_backward(gt.to_dev(g), grad)
+    assert ctx.gem_status() == 0
+    ref = oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g)
+    absum = oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g, absolute=True)
+    got = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    u = 2.0 ** -24
+    bound = 1e-5 * np.linalg.norm(ref, axis=1, keepdims=True) + 256 * u * absum
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
 
 
 def test_projection_tau_zero_every_pair():
