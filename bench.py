@@ -59,10 +59,10 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 # from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
 # valid while the rasteriser sources hash to the value they had then.
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "35377fa4740ccb04",
+    "source_sha256_16": "f546a0d7131f6408",
     "workload": "A2",
-    "raster_fwd": 261.132288e6 + 18.030336e6,
-    "raster_bwd": 419.187968e6 + 94.786560e6,
+    "raster_fwd": 261.421056e6 + 17.710592e6,
+    "raster_bwd": 421.672704e6 + 94.927616e6,
 }
 
 
