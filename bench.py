@@ -61,8 +61,8 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 CAPTURED_TRAFFIC = {
     "source_sha256_16": "f546a0d7131f6408",
     "workload": "A2",
-    "raster_fwd": 261.421056e6 + 17.710592e6,
-    "raster_bwd": 421.672704e6 + 94.927616e6,
+    "raster_fwd": 260.943104e6 + 18.117120e6,
+    "raster_bwd": 420.544512e6 + 94.433024e6,
 }
 
 

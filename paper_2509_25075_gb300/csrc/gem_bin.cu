@@ -518,14 +518,21 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
 // their tile; a hit's place in its tile's list is the tile's start, plus the
 // chunk's offset for that tile, plus the number of lower bits set (so the
 // list keeps the chunk's depth order).  Beside the Gaussian's index the
-// entry stores its 4x4-block mask.
+// entry stores its 4x4-block mask.  The chunk's Gaussian indices and the
+// list position of every tile it hits are staged first, so that each hit
+// costs one load of its own and two stores.
 __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     const uint32_t *__restrict__ perm, int64_t M, int d, int nch,
     const uint32_t *__restrict__ tcnt, const int64_t *__restrict__ tile_start, BinScratch bs) {
-  extern __shared__ uint32_t bm[];  // [T][8]
+  extern __shared__ __align__(16) uint32_t bm[];  // [T][8] bitmaps, then int64 list base [T]
+  __shared__ uint32_t sj[kChunkT];   // Gaussian index of each slot
   const int c = blockIdx.x, b = blockIdx.y;
   const int nt = d / kTile, T = nt * nt;
+  int64_t *tb = reinterpret_cast<int64_t *>(bm + T * 8);
   for (int i = threadIdx.x; i < T * 8; i += blockDim.x) bm[i] = 0;
+  const int64_t r0 = (int64_t)c * kChunkT;
+  if (r0 + threadIdx.x < M)
+    sj[threadIdx.x] = perm ? perm[(int64_t)b * M + r0 + threadIdx.x] : (uint32_t)(r0 + threadIdx.x);
   const int64_t hb = bs.chunk_base[(int64_t)b * nch + c];
   const int64_t hn = min((int64_t)bs.chunk_n[(int64_t)b * nch + c], max(bs.cap - hb, (int64_t)0));
   const int H = (int)hn;
@@ -537,8 +544,16 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     atomicOr(&bm[t * 8 + (o >> 5)], 1u << (o & 31));
   }
   __syncthreads();
+  // list base of every tile the chunk hits: the tile's start plus the
+  // chunk's offset in it
   const uint32_t *coff = tcnt + (int64_t)b * T * nch + c;
-  const int64_t r0 = (int64_t)c * kChunkT;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    uint32_t any = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) any |= bm[i * 8 + q];
+    if (any) tb[i] = tile_start[(int64_t)b * T + i] + coff[(int64_t)i * nch];
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     const uint64_t h = hr[i];
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
@@ -546,17 +561,18 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     const int word = o >> 5;
     uint32_t rank = __popc(bw[word] & ((1u << (o & 31)) - 1u));
     for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk]);
-    const int64_t pos = tile_start[(int64_t)b * T + t] + coff[(int64_t)t * nch] + rank;
+    const int64_t pos = tb[t] + rank;
     if (pos < bs.cap) {
-      bs.list[pos] = perm ? perm[(int64_t)b * M + r0 + o] : (uint32_t)(r0 + o);
+      bs.list[pos] = sj[o];
       bs.lmask[pos] = (uint16_t)(h >> 24);
     }
   }
 }
 
+// Bitmaps (8 words) and list base (8 bytes) per tile.
 static int tile_smem_bytes(int d) {
   int nt = d / kTile;
-  return nt * nt * 8 * (int)sizeof(uint32_t);
+  return nt * nt * (8 * (int)sizeof(uint32_t) + (int)sizeof(int64_t));
 }
 
 // The dynamic shared memory of both tile kernels (bitmaps, counters) is
