@@ -61,8 +61,8 @@ FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 CAPTURED_TRAFFIC = {
     "source_sha256_16": "f546a0d7131f6408",
     "workload": "A2",
-    "raster_fwd": 260.943104e6 + 18.117120e6,
-    "raster_bwd": 420.544512e6 + 94.433024e6,
+    "raster_fwd": 261.190912e6 + 17.378048e6,
+    "raster_bwd": 420.895488e6 + 95.129600e6,
 }
 
 

@@ -212,6 +212,8 @@ __device__ __forceinline__ RowGeo make_row_geo(const Rec &r, float l2tau) {
 // rounding step is explicit (no contraction the compiler could choose per
 // call site), so each inlined copy returns the same bits for the same input.
 constexpr unsigned kNoRow = 0x00ffu;  // lo = 255 > hi = 0
+// sqrt_approx with its product rounded on its own (never fused into a
+// neighbouring add)
 __device__ __forceinline__ float sqrt_rn_approx(float x) {
   x = fmaxf(x, 0.f);
   return __fmul_rn(x, rsqrtf(fmaxf(x, 1e-30f)));
@@ -243,7 +245,7 @@ __device__ __forceinline__ unsigned block_row_range(const RowGeo &G, int by, int
 // (Gaussian, candidate tile) items can be spread evenly over the threads
 // whatever the Gaussians' sizes.  Each block row's column range is computed
 // once and shared by every candidate tile of the Gaussian in that row.
-constexpr int kOwnerCap = 4096;  // candidates per chunk with a byte owner map
+constexpr int kOwnerCap = 2048;  // candidates per chunk with a byte owner map and cached masks
 constexpr int kRowCap = 2048;    // block rows per chunk whose ranges are staged
 
 struct ChunkStage {
@@ -254,6 +256,7 @@ struct ChunkStage {
   int roff[kChunkT + 1];   // exclusive prefix of block-row counts; roff[kChunkT] = rows
   int wsum[kChunkT / 32], wrow[kChunkT / 32];
   unsigned char owner[kOwnerCap];   // owner slot of each candidate (when they fit)
+  unsigned short cmask[kOwnerCap];  // block mask of each candidate (when they fit)
   unsigned char rowner[kRowCap];    // owner slot of each block row (when they fit)
   unsigned short rowx[kRowCap];     // block-row column ranges (when they fit)
 };
@@ -404,7 +407,9 @@ __global__ void __launch_bounds__(kChunkT, 8) tile_count_kernel(
     const int o = candidate_owner(S, k, total);
     int tx, ty;
     candidate_tile(S, o, k - S.off[o], tx, ty);
-    if (candidate_mask(S, staged, o, tx, ty, nb)) {
+    const unsigned m = candidate_mask(S, staged, o, tx, ty, nb);
+    if (total <= kOwnerCap) S.cmask[k] = (unsigned short)m;
+    if (m) {
       atomicAdd(&tc[ty * nt + tx], 1u);
       ++nh;
     }
@@ -431,13 +436,16 @@ __global__ void __launch_bounds__(kChunkT, 8) tile_count_kernel(
     bs.chunk_n[(int64_t)b * nch + c] = (uint32_t)H;
   }
   __syncthreads();
-  // the same candidates again, in the same order, with the same masks
+  // the same candidates again, in the same order, with the same masks (this
+  // thread's own cached ones, or computed again from the same inputs)
   int64_t dst = run_base + before;
   for (int k = threadIdx.x; k < total && nh > 0; k += kChunkT) {
+    const unsigned mc = total <= kOwnerCap ? S.cmask[k] : 1u;
+    if (!mc) continue;
     const int o = candidate_owner(S, k, total);
     int tx, ty;
     candidate_tile(S, o, k - S.off[o], tx, ty);
-    const unsigned m = candidate_mask(S, staged, o, tx, ty, nb);
+    const unsigned m = total <= kOwnerCap ? mc : candidate_mask(S, staged, o, tx, ty, nb);
     if (!m) continue;
     if (dst < bs.cap) bs.hits[dst] = pack_hit(o, ty * nt + tx, m);
     ++dst;

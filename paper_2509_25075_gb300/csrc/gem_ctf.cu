@@ -16,8 +16,10 @@
 // Three passes through a [B][d][d] complex buffer, stored transposed
 // (Z[b][kx][y]) so that every FFT runs on contiguous lines:
 //   pass 1: FFT along x of 16 rows of z, written transposed;
-//   pass 2: FFT along y of the lines kx and d - kx (8 pairs per CTA),
-//           CTF, loss, W, inverse FFT along y, written back in place;
+//   pass 2: FFT along y of the lines kx and d - kx (8 pairs per CTA; the
+//           first CTA holds the self-paired lines 0 and d/2 in the slots
+//           of line 0's pair), CTF, loss, W, inverse FFT along y, written
+//           back in place;
 //   pass 3: inverse FFT along x of 16 rows, split into I_pred and dL/dI^.
 // FFTs are radix-4/2/3 Stockham transforms in shared memory (d = 2^a 3^b).
 #include <math.h>
@@ -185,8 +187,16 @@ __device__ __forceinline__ float ctf_at(const CtfConst &c, int sx, int sy) {
 
 __device__ __forceinline__ int signed_bin(int k, int d) { return k < d / 2 ? k : k - d; }
 
-// pass 2: lines kx1 = 8 c + i (i < 8, kx1 <= d/2) and their partners
-// kx2 = (d - kx1) mod d.
+// Line kx held in slot i of pass-2 CTA blk (see ctf_pass2_kernel).
+__device__ __forceinline__ int pass2_line(int blk, int i, int d) {
+  const int kx1 = 8 * blk + (i & 7);
+  return i < 8 ? kx1 : (kx1 == 0 ? d / 2 : d - kx1);
+}
+
+// pass 2: slots i < 8 hold the lines kx1 = 8 c + i (kx1 < d/2), slots 8 + i
+// their partners d - kx1; line 0 is its own partner, so its slot 8 holds
+// the other self-paired line, d/2.  d is a multiple of 16, so the d/16
+// CTAs of an image hold every line once.
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     FftPlan pl, const float2 *__restrict__ tw, const float *__restrict__ ctf,
     const float *__restrict__ ctf_params, float apix, float2 *__restrict__ Z,
@@ -202,25 +212,20 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   if (ctf_params && threadIdx.x == 0) cc = ctf_const(ctf_params + 8 * b, d, apix);
   float2 *zb = Z + (int64_t)b * d * d;
   const float rd = 1.f / (float)d;
-  // load the 16 lines: i < 8 -> kx1, i >= 8 -> kx2
+  // load the 16 lines
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
-    int i = fdiv_small(idx, rd), y = idx - i * d;
-    int kx1 = 8 * blk + (i & 7);
-    float2 v = make_float2(0.f, 0.f);
-    if (kx1 <= hd) {
-      int kx = i < 8 ? kx1 : (kx1 == 0 ? 0 : d - kx1);
-      v = zb[(int64_t)kx * d + y];
-    }
-    a[i * ls + y] = v;
+    const int i = fdiv_small(idx, rd), y = idx - i * d;
+    a[i * ls + y] = zb[(int64_t)pass2_line(blk, i, d) * d + y];
   }
   __syncthreads();
   float2 *L = fft_lines(a, bb, kLines, pl, tws, ls);
-  // combine: thread per (pair i, ky)
+  // combine: thread per (pair i, ky); the first CTA has a ninth "pair", the
+  // self-paired line d/2 in slot 8
   float lsum = 0.f;
-  for (int idx = threadIdx.x; idx < 8 * d; idx += blockDim.x) {
+  const int npair = blk == 0 ? 9 : 8;
+  for (int idx = threadIdx.x; idx < npair * d; idx += blockDim.x) {
     int i = fdiv_small(idx, rd), ky = idx - i * d;
-    int kx = 8 * blk + i;
-    if (kx > hd) continue;
+    int kx = i < 8 ? 8 * blk + i : hd;
     bool self = (kx == 0 || kx == hd);
     if (self && ky > hd) continue;
     int mky = ky == 0 ? 0 : d - ky;
@@ -270,14 +275,9 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   float2 *other = (L == a) ? bb : a;
   float2 *R2 = fft_lines(L, other, kLines, pl, tws, ls);
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
-    int i = fdiv_small(idx, rd), y = idx - i * d;
-    int kx1 = 8 * blk + (i & 7);
-    if (kx1 > hd) continue;
-    bool self = (kx1 == 0 || kx1 == hd);
-    if (i >= 8 && self) continue;
-    int kx = i < 8 ? kx1 : d - kx1;
-    float2 v = R2[i * ls + y];
-    zb[(int64_t)kx * d + y] = make_float2(v.x, -v.y);
+    const int i = fdiv_small(idx, rd), y = idx - i * d;
+    const float2 v = R2[i * ls + y];
+    zb[(int64_t)pass2_line(blk, i, d) * d + y] = make_float2(v.x, -v.y);
   }
 }
 
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) loss_mean_kernel(const double *__restrict
   }
 }
 
-size_t ctf_partials(int d) { return (size_t)((d / 2 + 1 + 7) / 8); }
+size_t ctf_partials(int d) { return (size_t)(d / 16); }
 
 cudaError_t ctf_configure(int d) {
   int smem = (int)ctf_smem(d);

@@ -10,7 +10,7 @@
 // process exits.  The caller still passes its own inputs and outputs.
 //
 // Limits: B * d * d <= 1,048,576 spectrum elements (8 MiB), at most 65,536
-// loss partials (B * (ceil((d/2 + 1) / 8) + 1)), d as for gem_create.
+// loss partials (B * (d / 16 + 1)), d as for gem_create.
 #include <math.h>
 
 #include <mutex>

@@ -20,9 +20,9 @@ SMALL = [
     syn.Workload("s32w", d=32, M=301, B=2, apix=1.0, s_lo=0.3, s_hi=6.0, n_clusters=4, seed=13),
 ]
 # Gaussians so large that the first chunk of 256 (depth order) has more block
-# rows than the tile count stages (big96: about 3100 of 2048), and also more
-# candidate tiles than its byte owner map holds (big128: about 5100 of
-# 4096), while the second chunk fits both: both paths run in one binning.
+# rows (big96: about 3100, big128: 3900) and more candidate tiles (3600,
+# 5100) than the tile count stages (2048 of each), while the second chunk
+# fits both: the staged and the unstaged paths run in one binning.
 # Their lists need more than the default 16 entries per (image, Gaussian)
 # (big128: about 17), so their contexts get 64.
 LARGE = [
