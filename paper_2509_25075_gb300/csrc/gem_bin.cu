@@ -482,39 +482,53 @@ __global__ void __launch_bounds__(256) tile_scan_cols_kernel(uint32_t *__restric
 }
 
 // In-place exclusive scan of n counts (one block of 1024), total in x[n].
-// Flags the capacity bit when the total exceeds cap.
+// Flags the capacity bit when the total exceeds cap.  Each round scans 4096
+// counts as four consecutive runs of 1024 (one per sub-round q), with one
+// set of barriers; every thread keeps the running carry itself.
 __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ x, int64_t n,
                                                           int64_t cap, int *__restrict__ status) {
-  __shared__ int64_t wtot[32];
-  __shared__ int64_t carry;
+  constexpr int kQ = 4;
+  __shared__ int64_t wtot[kQ][32];  // per run: exclusive prefix of the warps' sums
+  __shared__ int64_t qtot[kQ];      // per run: its total
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < n; base += 1024) {
-    int64_t i = base + threadIdx.x;
-    int64_t v = i < n ? x[i] : 0;
-    int64_t inc = v;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += kQ * 1024) {
+    int64_t v[kQ], inc[kQ];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int64_t u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
+    for (int q = 0; q < kQ; ++q) {
+      const int64_t i = base + q * 1024 + threadIdx.x;
+      v[q] = i < n ? x[i] : 0;
     }
-    if (lane == 31) wtot[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-      int64_t w = wtot[lane], wi = w;
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      inc[q] = v[q];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += u;
+        const int64_t u = __shfl_up_sync(0xffffffffu, inc[q], o);
+        if (lane >= o) inc[q] += u;
       }
-      wtot[lane] = wi - w;  // exclusive prefix over warps
+      if (lane == 31) wtot[q][warp] = inc[q];
     }
     __syncthreads();
-    if (i < n) x[i] = carry + wtot[warp] + inc - v;
+    if (warp < kQ) {
+      const int64_t w = wtot[warp][lane];
+      int64_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      wtot[warp][lane] = wi - w;
+      if (lane == 31) qtot[warp] = wi;
+    }
     __syncthreads();
-    if (threadIdx.x == 1023) carry += wtot[31] + inc;
-    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      const int64_t i = base + q * 1024 + threadIdx.x;
+      if (i < n) x[i] = carry + wtot[q][warp] + inc[q] - v[q];
+      carry += qtot[q];
+    }
+    __syncthreads();  // wtot and qtot are read before the next round rewrites them
   }
   if (threadIdx.x == 0) {
     x[n] = carry;
