@@ -208,9 +208,23 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   Kahan GS[6], DP[3], M0;
   float inv = 1.f / apix;
   int b0 = bg * per_group, b1 = min(B, b0 + per_group);
+  // the next view's moments are loaded while this view's are used
+  float2 na = make_float2(0.f, 0.f), nb = na, nc = na;
+  if (b0 < b1) {
+    const float2 *m0p = reinterpret_cast<const float2 *>(mom + ((int64_t)b0 * M + j) * 6);
+    na = m0p[0];
+    nb = m0p[1];
+    nc = m0p[2];
+  }
   for (int b = b0; b < b1; ++b) {
     float2 *mm = reinterpret_cast<float2 *>(mom + ((int64_t)b * M + j) * 6);
-    const float2 ma = mm[0], mb = mm[1], mc = mm[2];
+    const float2 ma = na, mb = nb, mc = nc;
+    if (b + 1 < b1) {
+      const float2 *mn = reinterpret_cast<const float2 *>(mm + 3 * M);  // view b + 1
+      na = mn[0];
+      nb = mn[1];
+      nc = mn[2];
+    }
     float m0 = ma.x, m1 = ma.y, m2 = mb.x, m3 = mb.y, m4 = mc.x, m5 = mc.y;
     if (m0 == 0.f && m1 == 0.f && m2 == 0.f && m3 == 0.f && m4 == 0.f && m5 == 0.f) continue;
     // leave the moments cleared for the next backward pass
