@@ -73,3 +73,27 @@ def test_null_arguments():
     assert lib.gem_project(None, None, 1, 1, None, None, None) == binding.GEM_EINVAL
     assert lib.gem_backward(None, None) == binding.GEM_EINVAL
     assert lib.gem_last_error(None) == b""
+
+
+def test_static_ctf_step_validates_before_device_work():
+    """gem_ctf_loss_static checks its arguments and its fixed capacity before
+    any CUDA call; the pointers here are never dereferenced."""
+    lib = binding.load()
+    p = ctypes.c_void_p(1 << 20)  # 16-byte aligned stand-in address
+    odd = ctypes.c_void_p((1 << 20) + 4)
+
+    def call(d=64, apix=1.2, B=2, proj=p, ctf=None, prm=p, imgs=p, pred=None, dproj=None):
+        return lib.gem_ctf_loss_static(d, apix, B, proj, ctf, prm, imgs, pred, dproj, None, None, None)
+
+    assert call(d=40) == binding.GEM_EINVAL        # not a multiple of 16
+    assert call(d=80) == binding.GEM_EINVAL        # not 2^a 3^b
+    assert call(d=1024) == binding.GEM_EINVAL      # above 768
+    assert call(apix=0.0) == binding.GEM_EINVAL
+    assert call(apix=float("nan")) == binding.GEM_EINVAL
+    assert call(B=0) == binding.GEM_EINVAL
+    assert call(proj=None) == binding.GEM_EINVAL
+    assert call(prm=None) == binding.GEM_EINVAL    # no CTF
+    assert call(ctf=p) == binding.GEM_EINVAL       # both CTF forms
+    assert call(pred=odd) == binding.GEM_EINVAL    # misaligned output
+    assert call(d=256, B=17) == binding.GEM_ECAPACITY  # 17 * 256^2 > 2^20 spectrum elements
+    assert call(d=768, B=2) == binding.GEM_ECAPACITY
