@@ -380,7 +380,7 @@ __device__ __forceinline__ uint64_t pack_hit(int o, int t, unsigned mask) {
   return (uint64_t)o | ((uint64_t)t << 8) | ((uint64_t)mask << 24);
 }
 
-__global__ void __launch_bounds__(kChunkT, 8) tile_count_kernel(
+__global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ perm, int64_t M, int d,
     float l2tau, int nch, uint32_t *__restrict__ tcnt, BinScratch bs) {
   extern __shared__ uint32_t tc[];
