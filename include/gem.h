@@ -338,7 +338,12 @@ int gem_activate(gem_ctx *ctx, int64_t M, const float *raw, float *params);
  * beyond them the call returns GEM_ECAPACITY and launches nothing.  Other bad
  * arguments return GEM_EINVAL; CUDA failures GEM_ECUDA.
  * The first call on each device looks up the arrays' device addresses
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps them for the life of the process; make
+ * that first call before any stream capture, and do not use the entry point
+ * across a cudaDeviceReset (or any re-creation of the device's primary
+ * context), after which the arrays may sit at other addresses.
+ * A CUDA error already pending when the call starts (from the caller's own
+ * earlier work) is reported as GEM_ECUDA and left pending, not cleared.
  * Every call on a device shares the same arrays, which keep the last call's
  * contents (every call rewrites what it reads); calls that overlap on the
  * GPU (different streams, no ordering between them) race on them. */

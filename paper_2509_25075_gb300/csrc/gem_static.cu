@@ -43,7 +43,10 @@ StaticScratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
 // Device addresses of the static arrays on the current device (looked up on
-// the first call for that device).
+// the first call for that device and kept for the life of the process: a
+// cudaDeviceReset, or anything else that tears down and re-creates the
+// device's primary context, may load the module at other addresses, so the
+// entry point must not be used across one).
 cudaError_t static_scratch(int dev, StaticScratch &out) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   StaticScratch &s = g_scratch[dev];
@@ -86,6 +89,9 @@ extern "C" int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float
                                    const float *ctf, const float *ctf_params,
                                    const float *images, float *pred, float *dproj,
                                    double *loss_img, double *loss, void *cuda_stream) {
+  // an error left pending by the caller's own earlier work is reported and
+  // left in place (peeked, not cleared); after this point any error is ours
+  if (cudaPeekAtLastError() != cudaSuccess) return GEM_ECUDA;
   if (!static_d_ok(d) || !(apix > 0.f) || !isfinite(apix) || B < 1) return GEM_EINVAL;
   if (!proj || !images || (ctf == nullptr) == (ctf_params == nullptr)) return GEM_EINVAL;
   if (!aligned16(proj) || !aligned16(images) || !aligned16(pred) || !aligned16(dproj))

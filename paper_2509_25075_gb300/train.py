@@ -144,7 +144,7 @@ class Trainer:
         os.replace(tmp, path)
 
     def load(self, path: str):
-        self.load_state_dict(torch.load(path, weights_only=False))
+        self.load_state_dict(torch.load(path, weights_only=True))
 
     def close(self):
         self.ctx.close()

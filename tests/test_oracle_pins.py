@@ -336,6 +336,34 @@ def test_ctf_grid_from_params_is_symmetric():
     assert H[0, 0, 0] == pytest.approx(-float(prm[0, 5]), rel=1e-6)
 
 
+@pytest.mark.parametrize("d,apix", [(32, 1.3), (24, 0.9)])
+def test_ctf_grid_maps_bins_to_physical_frequencies(d, apix):
+    """Eq. loss applies the transfer function in Fourier space.  A real
+    grating with an integer number of periods across the box, along x (the
+    column index u), along y (the row index v) or a diagonal, is an
+    eigenfunction of that operator: the CTF grid built from parameters must
+    scale it by the transfer function evaluated at the grating's physical
+    frequency (n_x / (d apix), n_y / (d apix)) in 1/Angstrom.  The CTF is
+    astigmatic at an angle that is neither 0 nor a multiple of pi/4, so a
+    swapped axis, a dropped apix, a missing 1/d or an unsigned bin index each
+    change the value."""
+    prm = np.array([[1.6e4, 1.1e4, 0.61, 300.0, 2.7, 0.1, 0.2, 15.0]])
+    H = oracle.ctf_grid_from_params(prm, d, apix)
+    v, u = np.meshgrid(np.arange(d), np.arange(d), indexing="ij")
+    for nx, ny in [(3, 0), (0, 5), (4, -7), (-6, 2), (5, 5), (1, -3)]:
+        for phase in (0.0, 0.7):
+            grating = np.cos(2 * np.pi * (nx * u + ny * v) / d + phase)[None]
+            out = oracle.ctf_apply(H, grating)
+            h = oracle.ctf_value(prm[0], nx / (d * apix), ny / (d * apix))
+            np.testing.assert_allclose(out, h * grating, rtol=0, atol=1e-12)
+    # the pin discriminates: the swapped-axis and unsigned-bin readings give
+    # other values at the gratings used above
+    assert abs(oracle.ctf_value(prm[0], 4 / (d * apix), -7 / (d * apix))
+               - oracle.ctf_value(prm[0], -7 / (d * apix), 4 / (d * apix))) > 1e-3
+    assert abs(oracle.ctf_value(prm[0], 4 / (d * apix), -7 / (d * apix))
+               - oracle.ctf_value(prm[0], 4 / (d * apix), (d - 7) / (d * apix))) > 1e-3
+
+
 # ------------------------------------------------------------ gradients -----
 
 def _case(seed, M=3, B=2, d=8):

@@ -16,6 +16,7 @@ import pytest
 import torch
 
 import gemtest as gt
+import oracle
 from paper_2509_25075_gb300 import binding
 from paper_2509_25075_gb300 import synthetic as syn
 
@@ -26,9 +27,27 @@ def _p(x):
     return None if x is None else ctypes.c_void_p(x.data_ptr())
 
 
-@pytest.mark.parametrize("form", ["params", "array"])
-def test_static_matches_context_twice(form):
-    w = syn.Workload("static", d=64, M=10, B=3, apix=1.2, seed=77)
+def _oracle_check(w, proj, imgs, kw, out, sel):
+    """The FP64 oracle's loss, prediction and adjoint for the images sel,
+    with the tolerances of the float path."""
+    if "ctf_params" in kw:
+        H = oracle.ctf_grid_from_params(kw["ctf_params"].cpu().numpy()[sel], w.d, w.apix)
+    else:
+        H = oracle.ctf_grid_from_half(kw["ctf"].cpu().numpy()[sel])
+    _, opred, oli, og = oracle.loss(H, proj.cpu().numpy()[sel], imgs.cpu().numpy()[sel])
+    og = og * len(sel) / w.B  # the oracle's adjoint of the sub-batch carries 2 / (len(sel) d^2)
+    np.testing.assert_allclose(out["loss_img"].cpu().numpy()[sel], oli, rtol=1e-5)
+    p = out["pred"].cpu().numpy()[sel]
+    assert np.max(np.abs(p - opred)) <= 1e-5 * np.max(np.abs(opred))
+    g = out["dproj"].cpu().numpy()[sel]
+    assert np.max(np.abs(g - og)) <= 2e-6 * np.max(np.abs(og))
+
+
+# d = 256, B = 16 fills the spectrum array exactly (16 * 256^2 = 2^20
+# elements): the largest request the fixed arrays accept
+@pytest.mark.parametrize("form,d,B", [("params", 64, 3), ("array", 64, 3), ("params", 256, 16)])
+def test_static_matches_context_twice(form, d, B):
+    w = syn.Workload("static", d=d, M=10, B=B, apix=1.2, seed=77)
     lib = binding.load()
     proj = gt.to_dev(syn.smooth_field(w))
     imgs = gt.to_dev(syn.images(w))
@@ -60,6 +79,8 @@ def test_static_matches_context_twice(form):
         assert np.max(np.abs(out["pred"].cpu().numpy() - r)) <= 1e-5 * np.max(np.abs(r))
         r = ref["dproj"].cpu().numpy()
         assert np.max(np.abs(out["dproj"].cpu().numpy() - r)) <= 2e-6 * np.max(np.abs(r))
+    # and against the FP64 oracle directly (first, middle and last image)
+    _oracle_check(w, proj, imgs, kw, out, np.array(sorted({0, w.B // 2, w.B - 1})))
     ctx.close()
 
 
