@@ -89,9 +89,6 @@ extern "C" int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float
                                    const float *ctf, const float *ctf_params,
                                    const float *images, float *pred, float *dproj,
                                    double *loss_img, double *loss, void *cuda_stream) {
-  // an error left pending by the caller's own earlier work is reported and
-  // left in place (peeked, not cleared); after this point any error is ours
-  if (cudaPeekAtLastError() != cudaSuccess) return GEM_ECUDA;
   if (!static_d_ok(d) || !(apix > 0.f) || !isfinite(apix) || B < 1) return GEM_EINVAL;
   if (!proj || !images || (ctf == nullptr) == (ctf_params == nullptr)) return GEM_EINVAL;
   if (!aligned16(proj) || !aligned16(images) || !aligned16(pred) || !aligned16(dproj))
@@ -99,6 +96,9 @@ extern "C" int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float
   const int64_t nblk = (int64_t)ctf_partials(d);
   if ((int64_t)B * d * d > kStaticSpectrum || (int64_t)B * (nblk + 1) > kStaticLoss)
     return GEM_ECAPACITY;
+  // an error left pending by the caller's own earlier work is reported and
+  // left in place (peeked, not cleared); after this point any error is ours
+  if (cudaPeekAtLastError() != cudaSuccess) return GEM_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GEM_ECUDA;
   StaticScratch s;
