@@ -52,6 +52,9 @@ extern "C" {
 #define GEM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed                 */
 #define GEM_ESTATE (-4)    /* call order violated (backward before forward, ...)          */
 #define GEM_ECAPACITY (-5) /* returned by gem_status: the pair list overflowed max_pairs  */
+#define GEM_ETIMEOUT (-6)  /* reserved: a device-side wait ran out.  No kernel of this    */
+                           /* library waits on another (work is claimed from counters    */
+                           /* that never block), so no call returns it today.            */
 
 /* Device status bits reported by gem_status. */
 #define GEM_STATUS_CAPACITY 1
@@ -75,14 +78,21 @@ typedef struct gem_config {
                        /*    ignored and get zero gradient ("Isotropic Scaling", same table;   */
                        /*    the paper sets s_j to the nearest-neighbour distance, which       */
                        /*    gem_nn_distance computes)                                         */
+  int32_t tile;        /* side of the square pixel tiles the Gaussians are binned into: 16    */
+                       /*    (0 selects it; the rasterisers are built for 16 x 16 tiles of     */
+                       /*    4 x 4-pixel blocks, so any other value is GEM_EINVAL)             */
+  int32_t fp64_check;  /* 1: gem_forward and gem_backward compute in float64 (the FP64 check  */
+                       /*    mode below, on the same float arrays: inputs widened, pred and   */
+                       /*    grad rounded back to float, the loss a float64); 0: float32 path */
 } gem_config;
 
-/* Fill *cfg with defaults: tau = 0, norm_mode 0, zsort 1, max_pairs 0, no ablation. */
+/* Fill *cfg with defaults: tau = 0, norm_mode 0, zsort 1, max_pairs 0, no ablation,
+ * tile 16, fp64_check 0. */
 int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, int64_t max_M);
 
 /* Create a context.  cuda_stream is a cudaStream_t (NULL: the legacy default
  * stream).  Allocates all scratch on the current device: about
- * 32 B x max_B x max_M (projected records) + 24 B x max_B x max_M (moments)
+ * 32 B x max_B x max_M (projected records) + 48 B x max_B x max_M (moments)
  * + 4 B x max_pairs x 1 (lists) + 20 B x max_B x d^2 (images, spectra) and
  * a few small tables.  Errors: GEM_EINVAL, GEM_ENOMEM, GEM_ECUDA. */
 int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream);
@@ -146,9 +156,20 @@ int gem_ctf_loss(gem_ctx *ctx, int32_t B, const float *proj, const float *ctf,
  * Errors: GEM_ESTATE (no projection yet), GEM_EINVAL. */
 int gem_project_backward(gem_ctx *ctx, const float *dproj, float *grad);
 
+/* The Gaussians of the density representation (Eq. recon: the unknown the
+ * images are fitted to), [M][11] device float32, caller-owned.  The context
+ * keeps the pointer and M (no copy): gem_forward with params = NULL uses
+ * them, so they must stay valid and unchanged until that forward's
+ * gem_backward has been enqueued.  Errors: GEM_EINVAL (NULL, M outside
+ * 1..max_M). */
+int gem_set_gaussians(gem_ctx *ctx, const float *params, int64_t M);
+
 /* a1-a4 in one call: gem_project into the context's own image buffer, then
  * gem_ctf_loss with the adjoint kept inside the context for gem_backward.
- * pred may be NULL; loss is a device float64 [1]. */
+ * params = NULL: the Gaussians of the last gem_set_gaussians (M is then
+ * ignored; GEM_ESTATE if none were set).  pred may be NULL; loss is a device
+ * float64 [1].  With fp64_check the whole step runs in float64 (see the
+ * config field). */
 int gem_forward(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
                 const float *t, const float *ctf, const float *ctf_params, const float *images,
                 float *pred, double *loss);

@@ -63,6 +63,7 @@ def _load():
                 "gem_oracle_loss": (D, [I, I, P, P, P, P, P, P]),
                 "gem_oracle_grad": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
                 "gem_oracle_grad_abs": (None, [I, D, D, I, L, P, I, P, P, P, L, P, P]),
+                "gem_oracle_grad_border": (None, [I, D, D, I, L, P, I, P, P, P, L, P, D, P]),
                 "gem_oracle_query": (None, [I, D, D, I, L, P, P]),
                 "gem_oracle_query_voxels": (None, [I, D, D, I, L, P, L, P, P]),
             }
@@ -215,6 +216,27 @@ def grad(params, R, t, d, apix, tau, g, norm_mode: int = 0, sel=None, no_rotatio
     out = np.zeros((nsel, NPAR))
     fn = _load().gem_oracle_grad_abs if absolute else _load().gem_oracle_grad
     fn(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(g), nsel, selp, _ptr(out))
+    return out
+
+
+def grad_border(params, R, t, d, apix, tau, g, rel: float = 1e-5, norm_mode: int = 0,
+                sel=None) -> np.ndarray:
+    """[nsel][11]: sum of |g * dvalue/dtheta| over the (pixel, Gaussian) pairs
+    whose FP64 value lies within rel * tau of tau, kept or not.  These are the
+    pairs whose Eq. accu decision a float32 evaluation of the value may take
+    the other way, so this bounds the gradient difference such decisions
+    can make (test infrastructure; the projection's counterpart is tau per
+    borderline pair)."""
+    params, R, t, g = _f64(params), _f64(R), _f64(t), _f64(g)
+    M, B = params.shape[0], R.shape[0]
+    if sel is None:
+        nsel, selp = M, None
+    else:
+        sel_arr = np.ascontiguousarray(np.asarray(sel, dtype=np.int64))
+        nsel, selp = sel_arr.shape[0], _ptr(sel_arr)
+    out = np.zeros((nsel, NPAR))
+    _load().gem_oracle_grad_border(d, apix, tau, norm_mode, M, _ptr(params), B, _ptr(R), _ptr(t), _ptr(g),
+                                   nsel, selp, float(rel), _ptr(out))
     return out
 
 

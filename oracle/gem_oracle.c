@@ -485,28 +485,39 @@ double gem_oracle_loss(int d, int B, const double *hfull, const double *proj,
 /* ------------------------------------------------------------------------ */
 /* absolute != 0: the same loop summing |g * dvalue/dtheta| instead (the scale
  * against which the rounding error of a float sum of these terms is bounded;
- * test infrastructure, not part of the method). */
+ * test infrastructure, not part of the method).  border > 0: sum
+ * |g * dvalue/dtheta| over the pairs whose value lies within border * tau of
+ * tau, on either side (the pairs a float32 evaluation of Eq. accu may keep
+ * or drop differently from this double one; test infrastructure). */
 static void grad_loop(int d, double apix, double tau, int norm_mode, const double *params, int B,
                       const double *Rv, const double *tv, const double *g, int64_t nsel,
-                      const int64_t *sel, int absolute, double *grad);
+                      const int64_t *sel, int absolute, double border, double *grad);
 
 void gem_oracle_grad(int d, double apix, double tau, int norm_mode, int64_t M,
                      const double *params, int B, const double *Rv, const double *tv,
                      const double *g, int64_t nsel, const int64_t *sel, double *grad) {
   (void)M;
-  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 0, grad);
+  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 0, 0.0, grad);
 }
 
 void gem_oracle_grad_abs(int d, double apix, double tau, int norm_mode, int64_t M,
                          const double *params, int B, const double *Rv, const double *tv,
                          const double *g, int64_t nsel, const int64_t *sel, double *grad) {
   (void)M;
-  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 1, grad);
+  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 1, 0.0, grad);
+}
+
+void gem_oracle_grad_border(int d, double apix, double tau, int norm_mode, int64_t M,
+                            const double *params, int B, const double *Rv, const double *tv,
+                            const double *g, int64_t nsel, const int64_t *sel, double rel,
+                            double *grad) {
+  (void)M;
+  grad_loop(d, apix, tau, norm_mode, params, B, Rv, tv, g, nsel, sel, 1, rel, grad);
 }
 
 static void grad_loop(int d, double apix, double tau, int norm_mode, const double *params, int B,
                       const double *Rv, const double *tv, const double *g, int64_t nsel,
-                      const int64_t *sel, int absolute, double *grad) {
+                      const int64_t *sel, int absolute, double border, double *grad) {
   int64_t n = (int64_t)d * d;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t i = 0; i < nsel; ++i) {
@@ -520,7 +531,7 @@ static void grad_loop(int d, double apix, double tau, int norm_mode, const doubl
         for (int u = 0; u < d; ++u) {
           double x = pix_coord(u, d, apix), y = pix_coord(v, d, apix);
           double val = value_at(&pg, x, y);
-          if (!(val > tau)) continue;
+          if (border > 0.0 ? !(fabs(val - tau) <= border * tau) : !(val > tau)) continue;
           double gv = g[b * n + (int64_t)v * d + u] * val;
           double dx = x - pg.mean[0], dy = y - pg.mean[1];
           double w0 = pg.icov[0][0] * dx + pg.icov[0][1] * dy;

@@ -25,6 +25,7 @@ GEM_ENOMEM = -2
 GEM_ECUDA = -3
 GEM_ESTATE = -4
 GEM_ECAPACITY = -5
+GEM_ETIMEOUT = -6
 NPAR = 11
 
 
@@ -46,6 +47,8 @@ class gem_config(ctypes.Structure):
         ("zsort", ctypes.c_int32),
         ("no_rotation", ctypes.c_int32),
         ("isotropic", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+        ("fp64_check", ctypes.c_int32),
     ]
 
 
@@ -72,6 +75,7 @@ SIGNATURES = {
     "gem_project": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
     "gem_ctf_loss": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gem_project_backward": (ctypes.c_int, [_P, _P, _P]),
+    "gem_set_gaussians": (ctypes.c_int, [_P, _P, _I64]),
     "gem_forward": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P, _P]),
     "gem_backward": (ctypes.c_int, [_P, _P]),
     "gem_project_dense": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P]),
@@ -146,7 +150,7 @@ class Context:
 
     def __init__(self, d: int, apix: float, max_B: int, max_M: int, tau: float = 0.0,
                  norm_mode: int = 0, zsort: int = 1, max_pairs: int = 0, no_rotation: int = 0,
-                 isotropic: int = 0, stream=None):
+                 isotropic: int = 0, stream=None, fp64_check: int = 0, tile: int = 16):
         self.lib = load()
         cfg = gem_config()
         self.lib.gem_config_default(ctypes.byref(cfg), d, apix, max_B, max_M)
@@ -156,6 +160,8 @@ class Context:
         cfg.max_pairs = max_pairs
         cfg.no_rotation = no_rotation
         cfg.isotropic = isotropic
+        cfg.fp64_check = fp64_check
+        cfg.tile = tile
         self.cfg = cfg
         self.d, self.apix, self.max_B, self.max_M = d, apix, max_B, max_M
         self.device = torch.cuda.current_device()
@@ -170,6 +176,7 @@ class Context:
         self.B = None
         self.M64 = None
         self.B64 = None
+        self.set_M = None
 
     # -- plumbing ------------------------------------------------------------
     def _rc(self, rc):
@@ -240,8 +247,22 @@ class Context:
         _check(grad, "grad", (self.M, NPAR))
         self._rc(self.lib.gem_project_backward_dense(self.h, _ptr(dproj), _ptr(grad)))
 
+    def gem_set_gaussians(self, params):
+        M = params.shape[0]
+        _check(params, "params", (M, NPAR))
+        self._rc(self.lib.gem_set_gaussians(self.h, _ptr(params), M))
+        self.set_M = M
+
     def gem_forward(self, params, R, t, images, loss, ctf=None, ctf_params=None, pred=None):
-        M, B = self._views(params, R, t)
+        """params None: the Gaussians of the last gem_set_gaussians."""
+        if params is None:
+            if self.set_M is None:
+                raise GemError(GEM_ESTATE, "params None and no gem_set_gaussians")
+            M, B = self.set_M, R.shape[0]
+            _check(R, "R", (B, 3, 3))
+            _check(t, "t", (B, 2))
+        else:
+            M, B = self._views(params, R, t)
         d = self.d
         _check(images, "images", (B, d, d))
         _check(ctf, "ctf", (B, d, d // 2 + 1), optional=True)

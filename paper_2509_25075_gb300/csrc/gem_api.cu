@@ -29,7 +29,7 @@ struct gem_ctx {
   Rec *rec = nullptr;
 
   BinScratch bin{};
-  float *mom = nullptr;
+  double *mom = nullptr;   // [max_B][max_M][6] moments of the raster backward
   bool mom_clean = false;  // every moment is zero (prep_bwd leaves them so)
   float *part = nullptr;
   int nbg = 1;
@@ -56,7 +56,15 @@ struct gem_ctx {
     const double *params = nullptr, *R = nullptr, *t = nullptr;
     int64_t M = 0;
     int B = 0;
+    // fp64_check contexts: float inputs of gem_forward widened, and the
+    // step's float64 intermediates (allocated by gem_create)
+    double *params_in = nullptr, *R_in = nullptr, *t_in = nullptr, *images_in = nullptr;
+    double *ctf_in = nullptr, *proj = nullptr, *pred = nullptr, *dproj = nullptr, *grad = nullptr;
+    bool have_dproj = false;
   } f64;
+  // Gaussians given by gem_set_gaussians (used by gem_forward with params = NULL)
+  const float *set_params = nullptr;
+  int64_t set_M = 0;
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -157,8 +165,12 @@ int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, in
   cfg->zsort = 1;
   cfg->no_rotation = 0;
   cfg->isotropic = 0;
+  cfg->tile = kTile;
+  cfg->fp64_check = 0;
   return GEM_OK;
 }
+
+static int f64_scratch(gem_ctx *c);
 
 int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
   if (!out || !cfg) return GEM_EINVAL;
@@ -189,12 +201,18 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
     code = fail(c, GEM_EINVAL, "no_rotation must be 0 or 1");
   else if (g.isotropic != 0 && g.isotropic != 1)
     code = fail(c, GEM_EINVAL, "isotropic must be 0 or 1");
+  else if (g.tile != 0 && g.tile != kTile)
+    code = fail(c, GEM_EINVAL, "tile=%d: the rasterisers use %d x %d tiles (0 selects them)", g.tile,
+                kTile, kTile);
+  else if (g.fp64_check != 0 && g.fp64_check != 1)
+    code = fail(c, GEM_EINVAL, "fp64_check must be 0 or 1");
   if (code != GEM_OK) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", c->err);
     delete c;
     return code;
   }
   if (c->cfg.max_pairs == 0) c->cfg.max_pairs = 16 * (int64_t)g.max_B * g.max_M;
+  c->cfg.tile = kTile;
   const int d = g.d;
   c->T = (d / kTile) * (d / kTile);
   c->l2tau = g.tau > 0.f ? log2f(g.tau) : -INFINITY;
@@ -227,6 +245,15 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
        alloc(c, &c->knn.order, g.max_M) &&
        alloc(c, &c->knn.bsum, (size_t)knn_scan_blocks(c->knn.cap) + 1) &&
        alloc(c, &c->qp, g.max_M);
+  if (ok && g.fp64_check) {
+    const size_t n = (size_t)g.max_B * d * d;
+    ok = f64_scratch(c) == GEM_OK && alloc(c, &c->f64.params_in, (size_t)g.max_M * kNpar) &&
+         alloc(c, &c->f64.R_in, (size_t)g.max_B * 9) && alloc(c, &c->f64.t_in, (size_t)g.max_B * 2) &&
+         alloc(c, &c->f64.images_in, n) &&
+         alloc(c, &c->f64.ctf_in, (size_t)g.max_B * d * (d / 2 + 1)) &&
+         alloc(c, &c->f64.proj, n) && alloc(c, &c->f64.pred, n) && alloc(c, &c->f64.dproj, n) &&
+         alloc(c, &c->f64.grad, (size_t)g.max_M * kNpar);
+  }
   if (!ok) {
     snprintf(g_create_err, sizeof(g_create_err), "device allocation failed");
     gem_destroy(c);
@@ -398,7 +425,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
   const gem_config &g = c->cfg;
   cudaError_t e;
   // the whole buffer, should an earlier pass have stopped before clearing it
-  size_t mbytes = (size_t)g.max_B * g.max_M * 6 * sizeof(float);
+  size_t mbytes = (size_t)g.max_B * g.max_M * 6 * sizeof(double);
   {
     StageScope sc(c, GEM_STAGE_RASTER_BWD, 1);
     if (!dense && !c->mom_clean && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
@@ -427,6 +454,49 @@ int gem_project_backward_dense(gem_ctx *c, const float *dproj, float *grad) {
   return backward_common(c, dproj, grad, true);
 }
 
+int gem_set_gaussians(gem_ctx *c, const float *params, int64_t M) {
+  if (!c) return GEM_EINVAL;
+  if (!params) return fail(c, GEM_EINVAL, "null params");
+  if (M < 1 || M > c->cfg.max_M)
+    return fail(c, GEM_EINVAL, "M=%lld outside 1..max_M=%lld", (long long)M,
+                (long long)c->cfg.max_M);
+  c->set_params = params;
+  c->set_M = M;
+  return GEM_OK;
+}
+
+// gem_forward of an fp64_check context: the float inputs widened into the
+// context's float64 buffers, then the FP64 check-mode steps.
+static int forward_f64(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                       const float *t, const float *ctf, const float *ctf_params,
+                       const float *images, float *pred, double *loss) {
+  int rc = check_project_args(c, params, M, B, R, t, c->proj);
+  if (rc) return rc;
+  const gem_config &g = c->cfg;
+  const int64_t n = (int64_t)B * g.d * g.d;
+  c->f64.have_dproj = false;
+  cudaError_t e;
+  if ((e = launch_f64_widen(params, c->f64.params_in, M * kNpar, c->stream)) != cudaSuccess ||
+      (e = launch_f64_widen(R, c->f64.R_in, (int64_t)B * 9, c->stream)) != cudaSuccess ||
+      (e = launch_f64_widen(t, c->f64.t_in, (int64_t)B * 2, c->stream)) != cudaSuccess ||
+      (e = launch_f64_widen(images, c->f64.images_in, n, c->stream)) != cudaSuccess ||
+      (e = launch_f64_widen(ctf ? ctf : ctf_params, c->f64.ctf_in,
+                            ctf ? (int64_t)B * g.d * (g.d / 2 + 1) : (int64_t)B * 8, c->stream)) !=
+          cudaSuccess)
+    return cuda_fail(c, e, "fp64_check widen");
+  if ((rc = gem_project_f64(c, c->f64.params_in, M, B, c->f64.R_in, c->f64.t_in, c->f64.proj)))
+    return rc;
+  if ((rc = gem_ctf_loss_f64(c, B, c->f64.proj, ctf ? c->f64.ctf_in : nullptr,
+                             ctf ? nullptr : c->f64.ctf_in, c->f64.images_in,
+                             pred ? c->f64.pred : nullptr, c->f64.dproj, nullptr, loss)))
+    return rc;
+  if (pred && (e = launch_f64_narrow(c->f64.pred, pred, n, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "fp64_check narrow");
+  c->f64.have_dproj = true;
+  c->M = M;
+  return GEM_OK;
+}
+
 int gem_forward(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
                 const float *t, const float *ctf, const float *ctf_params, const float *images,
                 float *pred, double *loss) {
@@ -434,6 +504,14 @@ int gem_forward(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   if (!images) return fail(c, GEM_EINVAL, "null images");
   if ((ctf == nullptr) == (ctf_params == nullptr))
     return fail(c, GEM_EINVAL, "pass exactly one of ctf and ctf_params");
+  if (!params) {
+    if (!c->set_params) return fail(c, GEM_ESTATE, "params NULL and no gem_set_gaussians");
+    params = c->set_params;
+    M = c->set_M;
+  }
+  c->have_dproj = false;
+  if (c->cfg.fp64_check)
+    return forward_f64(c, params, M, B, R, t, ctf, ctf_params, images, pred, loss);
   int rc = gem_project(c, params, M, B, R, t, c->proj);
   if (rc) return rc;
   rc = gem_ctf_loss(c, B, c->proj, ctf, ctf_params, images, pred, c->dproj, nullptr, loss);
@@ -444,6 +522,15 @@ int gem_forward(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
 
 int gem_backward(gem_ctx *c, float *grad) {
   if (!c) return GEM_EINVAL;
+  if (c->cfg.fp64_check) {
+    if (!c->f64.have_dproj) return fail(c, GEM_ESTATE, "gem_backward needs a gem_forward first");
+    if (!grad) return fail(c, GEM_EINVAL, "null grad");
+    int rc = gem_project_backward_f64(c, c->f64.dproj, c->f64.grad);
+    if (rc) return rc;
+    cudaError_t e = launch_f64_narrow(c->f64.grad, grad, c->f64.M * kNpar, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fp64_check narrow");
+    return GEM_OK;
+  }
   if (!c->have_dproj) return fail(c, GEM_ESTATE, "gem_backward needs a gem_forward first");
   return gem_project_backward(c, c->dproj, grad);
 }

@@ -417,6 +417,29 @@ inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 
+// Array conversions of the check mode (float inputs widened, float outputs
+// narrowed; plain IEEE conversions, speed is not the point here).
+__global__ void f64_widen_kernel(const float *__restrict__ x, double *__restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+__global__ void f64_narrow_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+cudaError_t launch_f64_widen(const float *x, double *y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  f64_widen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_narrow(const double *x, float *y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  f64_narrow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_f64_project(const double *params, int64_t M, int B, const double *R,
                                const double *t, double apix, int d, int norm_mode, int shape,
                                double tau, G64 *gp, V64 *rec, double *proj, cudaStream_t st) {

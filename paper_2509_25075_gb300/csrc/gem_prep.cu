@@ -103,9 +103,15 @@ __global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restr
   View2D v = view_project(g, Rl, tl, apix, d);
   Rec r;
   float kap = v.l2A - l2tau;  // exponent headroom above the threshold
-  if (v.valid) {
-    r.a = make_float4(v.px, v.py, -0.5f * kLog2e * v.cxx, -kLog2e * v.cxy);
-    r.b = make_float4(-0.5f * kLog2e * v.cyy, v.l2A, -1.f, -1.f);
+  const float ca = -0.5f * kLog2e * v.cxx, cb = -kLog2e * v.cxy, cc = -0.5f * kLog2e * v.cyy;
+  // the exponent's quadratic form as stored must stay negative definite
+  // (4 ca cc > cb^2 in float32, the test the raster backward's S^ relies on):
+  // a Gaussian so elongated that rounding breaks this counts as degenerate
+  const float q = cb * cb, ql = fmaf(cb, cb, -q);
+  const bool definite = ca < 0.f && fmaf(4.f * ca, cc, -q) - ql > 0.f;
+  if (v.valid && definite) {
+    r.a = make_float4(v.px, v.py, ca, cb);
+    r.b = make_float4(cc, v.l2A, -1.f, -1.f);
     if (kap > 0.f) {
       // Q(d) = (log2 e / 2) d^T C d <= kappa + margin  =>
       //   |dx| <= sqrt((kappa + margin) * Sxx * 2 / log2 e), same for y
@@ -178,14 +184,15 @@ struct Kahan {
 };
 
 // Moments of one (view, Gaussian), accumulated by the raster backward over
-// the kept pixels (pixel units, dx = u - px, dy = v - py, val = 2D value,
-// g = dL/dproj):
-//   m0 = sum g val,  m1 = sum g val dx,  m2 = sum g val dy,
-//   m3 = sum g val dx^2,  m4 = sum g val dx dy,  m5 = sum g val dy^2.
-// From them (C = conic, S^ = its inverse, both pixel units):
+// the kept pixels in float64 (pixel units, dx = u - px, dy = v - py,
+// w = g * value, g = dL/dproj, S^ the projected covariance):
+//   m0 = sum w,  m1 = sum w dx,  m2 = sum w dy,
+//   N = [[m3, m4], [m4, m5]] = sum w (d d^T - S^).
+// From them (C = conic = S^^-1, pixel units):
 //   dL/dpx, dL/dpy = C (m1, m2)
-//   dL/dC  (matrix form, dL = tr(G_C dC)) = -1/2 [[m3, m4], [m4, m5]]
-//   dL/dS^ = -C G_C C - 1/2 m0 C          (C = S^^-1 and A ~ |S^|^-1/2)
+//   dL/dS^ = 1/2 C (sum w d d^T) C - 1/2 m0 C = 1/2 C N C
+//            (the conic's term and the amplitude's, A ~ |S^|^-1/2, already
+//             combined in N)
 //   dL/dSigma = R2^T dL/dS^ R2 / apix^2    (S^ = R2 Sigma R2^T / apix^2)
 //   dL/dp = R2^T (dL/dpx, dL/dpy) / apix
 //   dL/drho = m0 / rho;  mode 1 adds m0 / s_k to dL/ds_k.
@@ -194,7 +201,7 @@ struct Kahan {
 __global__ void __launch_bounds__(128) prep_bwd_kernel(
     const float *__restrict__ params, const GaussPrep *__restrict__ gp, int64_t M, int B,
     const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode, int shape,
-    float *__restrict__ mom, int per_group, float *__restrict__ part) {
+    double *__restrict__ mom, int per_group, float *__restrict__ part) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int bg = blockIdx.y;
   if (j >= M) return;
@@ -209,26 +216,30 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   float inv = 1.f / apix;
   int b0 = bg * per_group, b1 = min(B, b0 + per_group);
   // the next view's moments are loaded while this view's are used
-  float2 na = make_float2(0.f, 0.f), nb = na, nc = na;
+  longlong2 na = make_longlong2(0, 0), nb = na, nc = na;
   if (b0 < b1) {
-    const float2 *m0p = reinterpret_cast<const float2 *>(mom + ((int64_t)b0 * M + j) * 6);
+    const longlong2 *m0p = reinterpret_cast<const longlong2 *>(mom + ((int64_t)b0 * M + j) * 6);
     na = m0p[0];
     nb = m0p[1];
     nc = m0p[2];
   }
   for (int b = b0; b < b1; ++b) {
-    float2 *mm = reinterpret_cast<float2 *>(mom + ((int64_t)b * M + j) * 6);
-    const float2 ma = na, mb = nb, mc = nc;
+    longlong2 *mm = reinterpret_cast<longlong2 *>(mom + ((int64_t)b * M + j) * 6);
+    const longlong2 ma = na, mb = nb, mc = nc;
     if (b + 1 < b1) {
-      const float2 *mn = reinterpret_cast<const float2 *>(mm + 3 * M);  // view b + 1
+      const longlong2 *mn = mm + 3 * M;  // view b + 1
       na = mn[0];
       nb = mn[1];
       nc = mn[2];
     }
-    float m0 = ma.x, m1 = ma.y, m2 = mb.x, m3 = mb.y, m4 = mc.x, m5 = mc.y;
-    if (m0 == 0.f && m1 == 0.f && m2 == 0.f && m3 == 0.f && m4 == 0.f && m5 == 0.f) continue;
+    // all six zero (bit patterns: no FP64 compare): the Gaussian has no
+    // kept pixel in this view
+    if ((ma.x | ma.y | mb.x | mb.y | mc.x | mc.y) == 0) continue;
     // leave the moments cleared for the next backward pass
-    mm[0] = mm[1] = mm[2] = make_float2(0.f, 0.f);
+    mm[0] = mm[1] = mm[2] = make_longlong2(0, 0);
+    const float m0 = f64_to_f32(__longlong_as_double(ma.x)), m1 = f64_to_f32(__longlong_as_double(ma.y));
+    const float m2 = f64_to_f32(__longlong_as_double(mb.x)), m3 = f64_to_f32(__longlong_as_double(mb.y));
+    const float m4 = f64_to_f32(__longlong_as_double(mc.x)), m5 = f64_to_f32(__longlong_as_double(mc.y));
     float Rl[9], tl[2];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);
@@ -239,17 +250,13 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
     // d/dp^ (pixel units)
     float gpx = v.cxx * m1 + v.cxy * m2;
     float gpy = v.cxy * m1 + v.cyy * m2;
-    // G_C = -1/2 [[m3, m4], [m4, m5]];  T = C G_C C
-    float gxx = -0.5f * m3, gxy = -0.5f * m4, gyy = -0.5f * m5;
-    float u_xx = v.cxx * gxx + v.cxy * gxy, u_xy = v.cxx * gxy + v.cxy * gyy;
-    float u_yx = v.cxy * gxx + v.cyy * gxy, u_yy = v.cxy * gxy + v.cyy * gyy;
-    float t_xx = u_xx * v.cxx + u_xy * v.cxy;
-    float t_xy = u_xx * v.cxy + u_xy * v.cyy;
-    float t_yy = u_yx * v.cxy + u_yy * v.cyy;
-    // dL/dS^ (symmetric, matrix form)
-    float hxx = -t_xx - 0.5f * m0 * v.cxx;
-    float hxy = -t_xy - 0.5f * m0 * v.cxy;
-    float hyy = -t_yy - 0.5f * m0 * v.cyy;
+    // dL/dS^ = 1/2 C N C (symmetric, matrix form); U = 1/2 C N
+    float nxx = 0.5f * m3, nxy = 0.5f * m4, nyy = 0.5f * m5;
+    float u_xx = v.cxx * nxx + v.cxy * nxy, u_xy = v.cxx * nxy + v.cxy * nyy;
+    float u_yx = v.cxy * nxx + v.cyy * nxy, u_yy = v.cxy * nxy + v.cyy * nyy;
+    float hxx = u_xx * v.cxx + u_xy * v.cxy;
+    float hxy = u_xx * v.cxy + u_xy * v.cyy;
+    float hyy = u_yx * v.cxy + u_yy * v.cyy;
     // dL/dSigma = R2^T H R2 / apix^2
     float i2 = inv * inv;
     float r0[3] = {Rl[0], Rl[1], Rl[2]}, r1[3] = {Rl[3], Rl[4], Rl[5]};
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__
 
 cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
                             const float *R, const float *t, float apix, int d, int norm_mode,
-                            int shape, float *mom, float *part, int nbg, float *grad,
+                            int shape, double *mom, float *part, int nbg, float *grad,
                             cudaStream_t st) {
   int per = (B + nbg - 1) / nbg;
   int groups = (B + per - 1) / per;

@@ -23,11 +23,17 @@
 //     not yet taken), sorts the window by block count and runs it in rounds
 //     of 16 records with neighbouring counts, two lanes per record (two
 //     pixel rows of each block each): the lanes walk the record's blocks and
-//     accumulate six moments of g * value in registers (per row: the sums
-//     of w, w dx, w dx^2 in packed float pairs, weighted by dy), then add
-//     their halves.  No barrier couples the warps.  a6 turns
-//     the moments into parameter gradients.  One set of vector atomics per
-//     (tile, Gaussian) goes to global memory.
+//     accumulate six moments of w = g * value (per row: the sums of w, w dx,
+//     w dx^2 in packed float pairs, weighted by dy).  The second moments are
+//     taken about the record's projected covariance S^, sum w (d d^T - S^):
+//     for a wide Gaussian under a smooth upstream gradient the conic and
+//     amplitude terms of dL/dS^ nearly cancel, and this form lets that
+//     cancellation happen inside an accurate sum instead of in the float32
+//     chain rule.  Each block's sums join the lane's totals with Kahan
+//     compensation; the two lanes add their halves, and the (tile, Gaussian)
+//     partial goes to float64 moments in global memory (L2 atomics), so the
+//     sum over a Gaussian's tiles is exact to float64.  No barrier couples
+//     the warps.  a6 turns the moments into parameter gradients.
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -279,7 +285,7 @@ template <int kLpr, int kPer>
 __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
-    int64_t M, int d, float l2tau, const float *__restrict__ dproj, float *__restrict__ mom) {
+    int64_t M, int d, float l2tau, const float *__restrict__ dproj, double *__restrict__ mom) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kWW = 32 * kPer;     // records per warp window
   constexpr int kRpr = 32 / kLpr;    // records per round
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   e = min(e, cap);
   s = min(s, e);
   const Rec *rb = rec + (int64_t)b * M;
-  float *mb = mom + (int64_t)b * M * 6;
+  double *mb = mom + (int64_t)b * M * 6;
   int *h = hist[warp];
   const int gq = lane % kLpr;                                   // lane within the record's group
   const unsigned gmask = ((1u << kLpr) - 1u) << (lane - gq);    // the group's lanes
@@ -371,7 +377,15 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       const float2 Bv = sb[warp][slot];
       const float2 ca2 = f2(A.z);
       const float cb = A.w, cc = Bv.x, l2A = Bv.y;
-      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
+      // S^ of the record: the inverse of the conic its exponent evaluates,
+      // C = -2 ln2 [[ca, cb/2], [cb/2, cc]], so S^ = log2(e) / D
+      // [[-2 cc, cb], [cb, -2 ca]] with D = 4 ca cc - cb^2 (cb^2 split
+      // exactly, so D keeps its digits for elongated Gaussians)
+      const float cb2 = cb * cb, cb2l = fmaf(cb, cb, -cb2);
+      const float rD = kLog2e / (fmaf(4.f * A.z, cc, -cb2) - cb2l);
+      const float sxx = -2.f * cc * rD, sxy = cb * rD, syy = -2.f * A.z * rD;
+      float2 s01 = make_float2(0.f, 0.f), s23 = s01, s45 = s01;  // Kahan sums: (n0, n1), (n2, n3), (n4, n5)
+      float2 c01 = s01, c23 = s01, c45 = s01;                    // and their compensations
       for (unsigned mm = mk; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
         const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
@@ -379,6 +393,8 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
         const float2 dx01 = make_float2(fx, fx + 1.f);
         const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
         const float2 dxx01 = mul2(dx01, dx01), dxx23 = mul2(dx23, dx23);
+        // this block's rows: sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
 #pragma unroll
         for (int rr = 0; rr < kRows; ++rr) {
           const float dy = fy + (float)rr;
@@ -407,7 +423,16 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
           m4 = fmaf(r1, dy, m4);
           m5 = fmaf(r0 * dy, dy, m5);
         }
+        // second moments about S^, then into the lane's compensated totals
+        m3 = fmaf(-sxx, m0, m3);
+        m4 = fmaf(-sxy, m0, m4);
+        m5 = fmaf(-syy, m0, m5);
+        kahan2(s01, c01, make_float2(m0, m1));
+        kahan2(s23, c23, make_float2(m2, m3));
+        kahan2(s45, c45, make_float2(m4, m5));
       }
+      float m0 = s01.x - c01.x, m1 = s01.y - c01.y, m2 = s23.x - c23.x;
+      float m3 = s23.y - c23.y, m4 = s45.x - c45.x, m5 = s45.y - c45.y;
 #pragma unroll
       for (int o = 1; o < kLpr; o <<= 1) {
         m0 += __shfl_xor_sync(gmask, m0, o);
@@ -418,10 +443,13 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
         m5 += __shfl_xor_sync(gmask, m5, o);
       }
       if (gq == 0) {
-        float2 *mo = reinterpret_cast<float2 *>(mb + (int64_t)sj[warp][slot] * 6);
-        atomicAdd(mo + 0, make_float2(m0, m1));
-        atomicAdd(mo + 1, make_float2(m2, m3));
-        atomicAdd(mo + 2, make_float2(m4, m5));
+        double *mo = mb + (int64_t)sj[warp][slot] * 6;
+        atomicAdd(mo + 0, f32_to_f64(m0));
+        atomicAdd(mo + 1, f32_to_f64(m1));
+        atomicAdd(mo + 2, f32_to_f64(m2));
+        atomicAdd(mo + 3, f32_to_f64(m3));
+        atomicAdd(mo + 4, f32_to_f64(m4));
+        atomicAdd(mo + 5, f32_to_f64(m5));
       }
     }
     int wn = 0;
@@ -432,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
 
 cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, const float *dproj, float *mom, cudaStream_t st) {
+                              float l2tau, const float *dproj, double *mom, cudaStream_t st) {
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
   raster_bwd_kernel<kBwdLanes, kBwdPer><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start,
@@ -468,17 +496,21 @@ __global__ void __launch_bounds__(256) dense_fwd_kernel(const Rec *__restrict__ 
   if (act) proj[(int64_t)b * d * d + pix] = (float)acc;
 }
 
-// One thread per (image, Gaussian), every pixel of the image.
+// One thread per (image, Gaussian), every pixel of the image; the same six
+// moments as the tiled backward (second moments about S^, taken per row).
 __global__ void __launch_bounds__(128) dense_bwd_kernel(const Rec *__restrict__ rec, int64_t M,
                                                         int d, float l2tau,
                                                         const float *__restrict__ dproj,
-                                                        float *__restrict__ mom) {
+                                                        double *__restrict__ mom) {
   int b = blockIdx.y;
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   Rec r = rec[(int64_t)b * M + j];
   const float *g = dproj + (int64_t)b * d * d;
   float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float q = r.a.w * r.a.w, ql = fmaf(r.a.w, r.a.w, -q);
+  const float rD = kLog2e / (fmaf(4.f * r.a.z, r.b.x, -q) - ql);
+  const float sxx = -2.f * r.b.x * rD, sxy = r.a.w * rD, syy = -2.f * r.a.z * rD;
   for (int v = 0; v < d; ++v) {
     float dy = (float)v - r.a.y;
     float bdy = r.a.w * dy, cdy = fmaf(r.b.x * dy, dy, r.b.y);
@@ -496,13 +528,17 @@ __global__ void __launch_bounds__(128) dense_bwd_kernel(const Rec *__restrict__ 
     m[0] += r0;
     m[1] += r1;
     m[2] = fmaf(dy, r0, m[2]);
-    m[3] += r3;
-    m[4] = fmaf(dy, r1, m[4]);
-    m[5] = fmaf(dy * dy, r0, m[5]);
+    m[3] += fmaf(-sxx, r0, r3);
+    m[4] += fmaf(dy, r1, -sxy * r0);
+    m[5] = fmaf(fmaf(dy, dy, -syy), r0, m[5]);
   }
-  float *mm = mom + ((int64_t)b * M + j) * 6;
+  if (!(r.b.z >= 0.f)) {  // no region above tau: no tile, no moments
 #pragma unroll
-  for (int k = 0; k < 6; ++k) mm[k] = m[k];
+    for (int k = 0; k < 6; ++k) m[k] = 0.f;
+  }
+  double *mm = mom + ((int64_t)b * M + j) * 6;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) mm[k] = f32_to_f64(m[k]);
 }
 
 cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2tau, float *proj,
@@ -513,7 +549,7 @@ cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2ta
 }
 
 cudaError_t launch_dense_bwd(const Rec *rec, int64_t M, int B, int d, float l2tau,
-                             const float *dproj, float *mom, cudaStream_t st) {
+                             const float *dproj, double *mom, cudaStream_t st) {
   dim3 grid((unsigned)((M + 127) / 128), B);
   dense_bwd_kernel<<<grid, 128, 0, st>>>(rec, M, d, l2tau, dproj, mom);
   return cudaGetLastError();

@@ -20,9 +20,17 @@ def _declared():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for n in ["gem_create", "gem_destroy", "gem_project", "gem_ctf_loss", "gem_project_backward",
-              "gem_forward", "gem_backward", "gem_status", "gem_last_error"]:
+    # the calls of the hot path's C boundary (create, set the Gaussians,
+    # forward, backward, destroy, errors) and the stage calls
+    for n in ["gem_create", "gem_destroy", "gem_set_gaussians", "gem_project", "gem_ctf_loss",
+              "gem_project_backward", "gem_forward", "gem_backward", "gem_status", "gem_last_error"]:
         assert n in names
+    src = open(os.path.join(ROOT, "include", "gem.h")).read()
+    for code in ["GEM_EINVAL", "GEM_ENOMEM", "GEM_ECUDA", "GEM_ETIMEOUT", "GEM_ESTATE", "GEM_ECAPACITY"]:
+        assert re.search(r"#define " + code + r" \(-\d\)", src), code
+    for field in ["d", "apix", "tau", "tile", "norm_mode", "no_rotation", "isotropic", "fp64_check",
+                  "max_M", "max_B"]:
+        assert field in dict(binding.gem_config._fields_), field
 
 
 def test_library_exports_every_declared_symbol():
@@ -37,6 +45,7 @@ def _create(**over):
     cfg = binding.gem_config()
     assert lib.gem_config_default(ctypes.byref(cfg), 64, 1.2, 4, 100) == 0
     assert (cfg.d, cfg.max_B, cfg.max_M, cfg.zsort, cfg.norm_mode) == (64, 4, 100, 1, 0)
+    assert (cfg.tile, cfg.fp64_check) == (16, 0)
     for k, v in over.items():
         setattr(cfg, k, v)
     h = ctypes.c_void_p()
@@ -57,6 +66,8 @@ def _create(**over):
     ("zsort", 3, "zsort"),
     ("no_rotation", 2, "no_rotation"),
     ("isotropic", -1, "isotropic"),
+    ("tile", 8, "tile"),
+    ("fp64_check", 2, "fp64_check"),
 ])
 def test_bad_config_is_rejected_before_device_work(field, value, msg):
     rc, err, h = _create(**{field: value})
@@ -72,6 +83,7 @@ def test_null_arguments():
     assert lib.gem_status(None) == binding.GEM_EINVAL
     assert lib.gem_project(None, None, 1, 1, None, None, None) == binding.GEM_EINVAL
     assert lib.gem_backward(None, None) == binding.GEM_EINVAL
+    assert lib.gem_set_gaussians(None, None, 1) == binding.GEM_EINVAL
     assert lib.gem_last_error(None) == b""
 
 

@@ -449,6 +449,36 @@ def test_absolute_gradient_terms():
         assert A[j, 10] == pytest.approx(np.sum(np.abs(g) * img_j) / th[j, 10], rel=1e-12, abs=1e-18)
 
 
+def test_borderline_gradient_terms():
+    """grad_border sums |g dvalue/dtheta| over exactly the pairs whose value
+    lies within rel * tau of tau, on either side.  With tau set to the value
+    of one pixel of a single-Gaussian, single-view case, that pixel alone
+    qualifies, so the sum equals the absolute gradient of a unit upstream
+    gradient at that pixel (computed with tau = 0, where every pair counts);
+    a band wide enough to hold every value gives the tau = 0 absolute sums,
+    and a Gaussian whose peak stays below the band gives zero."""
+    th, Rv, t, imgs, H, d, apix = _case(26, M=3, B=1)
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=(1, d, d))
+    for j in range(3):
+        one = th[j:j + 1]
+        img = oracle.project(one, Rv, t, d, apix, 0.0)[0]
+        v, u = np.unravel_index(np.argsort(img, axis=None)[-5], img.shape)  # a pixel below the peak
+        tau = img[v, u]
+        others = np.abs(img - tau) <= 1e-9 * tau
+        assert others.sum() == 1  # that pixel alone sits in the band
+        delta = np.zeros((1, d, d))
+        delta[0, v, u] = abs(g[0, v, u])
+        want = np.abs(oracle.grad(one, Rv, t, d, apix, 0.0, delta * np.sign(g[0, v, u])))
+        got = oracle.grad_border(one, Rv, t, d, apix, tau, g, rel=1e-9)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+    everything = oracle.grad_border(th, Rv, t, d, apix, 1e-6, g, rel=1e300)
+    np.testing.assert_allclose(everything, oracle.grad(th, Rv, t, d, apix, 0.0, g, absolute=True),
+                               rtol=1e-13, atol=0)
+    peak = oracle.project(th[:1], Rv, t, d, apix, 0.0).max()
+    assert np.all(oracle.grad_border(th[:1], Rv, t, d, apix, 2 * peak, g, rel=1e-5) == 0)
+
+
 def test_gradient_selection_matches_full():
     th, Rv, t, imgs, H, d, apix = _case(24, M=5)
     proj = oracle.project(th, Rv, t, d, apix, 1e-3)
