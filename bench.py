@@ -2,20 +2,26 @@
 full step (projection a1-a3, CTF + loss + adjoint a4, sparse gradient a5-a6)
 on the synthetic stand-in for the paper's workloads.
 
-  python bench.py --gpus N --steps K --warmup W [--impl gem|reference]
+  python bench.py --gpus N --steps K --warmup W [--impl gem|reference] [--workload A5]
 
-Prints one JSON line on rank 0.  Under torchrun every rank runs an
-independent replica on its own GPU (its own batch): the method's images are
-independent, so the step shards with no data-path collective ("weak"
-scaling); value = images of all ranks / the slowest rank's time.
+Prints one JSON line on rank 0.  The default workload is A5 (d = 384,
+M = 500,000 Gaussians, 16 images per step), the largest configuration; A2 is
+also timed on the device and reported under ``secondary``.  Under torchrun
+every rank runs an independent replica on its own GPU (its own batch): the
+method's images are independent, so the step shards with no data-path
+collective ("weak" scaling); value = images of all ranks / the slowest
+rank's time.
 
 Timing: W untimed warm-up steps, the end-to-end loop, then K steps back to
 back, each bracketed by CUDA events on the library's stream with an L2 flush
 (a 256 MB write) between steps, outside the events; barrier + synchronize on
 both sides of the timed region; max over ranks.  The per-stage times come
-from a separate pass with the library's stage events on.  The ``e2e`` figure repeats the step through the public API
-with the step's inputs copied from pinned host memory and the loss and
-gradient copied back inside the timed region.
+from a separate pass with the library's stage events on.  The ``e2e`` figure
+repeats the step through the public API with the step's inputs copied from
+pinned host memory and the loss and gradient copied back inside the timed
+region.  After the timed region, ``parity`` states the step's error against
+the FP64 oracle on sampled outputs (projected pixels, per-image losses,
+sampled Gaussians' gradients), each beside its tolerance.
 """
 from __future__ import annotations
 
@@ -53,16 +59,20 @@ FP32_PER_CLK_PER_SM = 128
 #   backward (moments of g * value): dx, dy, exponent (7); w = g * value (1);
 #     the six moments w {1, dx, dy, dx^2, dx dy, dy^2}: 3 products, 5 adds or
 #     fused adds (8)                                                     -> 16
+# The roofline's `frac` uses these counts.  Counting every FP32 operation of
+# the direct evaluation instead (the compare and the exponent's scale as
+# well: about 10 forward, 30 backward) raises the peak's denominator less and
+# gives larger fractions; the line reports those too (`frac_all_fp32_ops`).
 FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
+ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 
-# DRAM bytes (read + write) per launch of each rasteriser at workload A2,
-# from the ncu capture summarised in profiles/rasterisers_and_binning_A2.md,
-# valid while the rasteriser sources hash to the value they had then.
+# DRAM bytes (read + write) per launch of each rasteriser, per workload, from
+# one ncu capture of that workload's bench step (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid while the rasteriser sources hash to the
+# value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "f546a0d7131f6408",
-    "workload": "A2",
-    "raster_fwd": 261.190912e6 + 17.378048e6,
-    "raster_bwd": 420.895488e6 + 95.129600e6,
+    "source_sha256_16": None,
+    "per_workload": {},
 }
 
 
@@ -99,7 +109,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gem", "reference"], default="gem")
-    ap.add_argument("--workload", default="A2")
+    ap.add_argument("--workload", default="A5")
+    ap.add_argument("--secondary", default="A2",
+                    help="comma-separated workloads also timed on the device (N=1 only; '' for none)")
+    ap.add_argument("--no-parity", action="store_true", help="skip the sampled check against the oracle")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain dense form")
     ap.add_argument("--no-query", action="store_true",
                     help="skip timing the density query, FSC, training iteration and nearest neighbours")
@@ -208,9 +221,14 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle ------
 
-def oracle_sample(w, n_images: int, seed: int = 0):
-    """Time the FP64 oracle on n_images images of workload w (full M and d).
-    Returns (seconds, images, threads)."""
+# Full images are timed when one costs the oracle at most this many
+# (pixel, Gaussian) evaluations (d^2 M); larger workloads are sampled.
+FULL_IMAGE_EVALS = 5e8
+
+
+def oracle_full(w, n_images: int, seed: int = 0):
+    """Time the FP64 oracle on n_images whole images of workload w (full M
+    and d).  Returns (seconds per image, threads, description)."""
     import oracle
     from paper_2509_25075_gb300 import synthetic as syn
 
@@ -224,24 +242,80 @@ def oracle_sample(w, n_images: int, seed: int = 0):
     _, _, _, g = oracle.loss(H, proj, inp["images"])
     oracle.grad(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau, g, w.norm_mode)
     dt = time.perf_counter() - t0
-    return dt, n_images, oracle.num_threads()
+    return dt / n_images, dt, oracle.num_threads(), (
+        f"{n_images} whole image(s) of workload {w.name} (d={w.d}, M={w.M}) through projection, "
+        f"CTF + loss + adjoint and the full gradient, FP64 brute force")
+
+
+def oracle_sampled(w, seed: int = 0, n_pix: int = 256, n_sel: int = 256):
+    """Time the FP64 oracle on a bounded sample of one image of workload w and
+    extrapolate to the whole image: the projection at n_pix pixels (each
+    against all M Gaussians), the CTF + loss + adjoint of one d x d image,
+    the gradient of n_sel Gaussians (each over all d^2 pixels).  Seconds per
+    image = t_pix d^2 / n_pix + t_ctf + t_grad M / n_sel."""
+    import numpy as np
+
+    import oracle
+    from paper_2509_25075_gb300 import synthetic as syn
+
+    sub = syn.Workload(w.name, d=w.d, M=w.M, B=1, apix=w.apix, s_lo=w.s_lo, s_hi=w.s_hi,
+                       n_clusters=w.n_clusters, seed=w.seed)
+    inp = syn.batch(sub, seed=seed)
+    params = syn.gaussians(w)
+    rng = np.random.default_rng(seed)
+    pix = rng.choice(w.d * w.d, size=n_pix, replace=False)
+    sel = rng.choice(w.M, size=n_sel, replace=False)
+    t0 = time.perf_counter()
+    oracle.project_pixels(params, inp["R"], inp["t"], w.d, w.apix, w.tau, pix, w.norm_mode)
+    t1 = time.perf_counter()
+    # the CTF step's cost does not depend on the image's content: a stand-in
+    # projection of the right size
+    H = oracle.ctf_grid_from_params(inp["ctf_params"], w.d, w.apix)
+    _, _, _, g = oracle.loss(H, syn.smooth_field(sub, seed=seed), inp["images"])
+    t2 = time.perf_counter()
+    oracle.grad(params, inp["R"], inp["t"], w.d, w.apix, w.tau, g, w.norm_mode, sel=sel)
+    t3 = time.perf_counter()
+    per_image = (t1 - t0) * w.d * w.d / n_pix + (t2 - t1) + (t3 - t2) * w.M / n_sel
+    return per_image, t3 - t0, oracle.num_threads(), (
+        f"workload {w.name} (d={w.d}, M={w.M}), one image sampled and extrapolated: projection at "
+        f"{n_pix} pixels x {w.M} Gaussians, CTF + loss + adjoint of one {w.d}x{w.d} image, gradient of "
+        f"{n_sel} Gaussians over all pixels; FP64 brute force")
+
+
+def oracle_per_image(w, seed: int = 0):
+    """(seconds per image, wall seconds spent, threads, description)."""
+    if w.d * w.d * w.M <= FULL_IMAGE_EVALS:
+        return oracle_full(w, 1, seed)
+    return oracle_sampled(w, seed)
 
 
 def cpu_baseline(w, budget_s: float = 15.0):
-    dt1, n1, thr = oracle_sample(w, 1)
-    n = max(1, min(16, int(budget_s / max(dt1, 1e-3))))
-    if n > 1:
-        dt, n, thr = oracle_sample(w, n, seed=1)
+    """The oracle on the host cores: whole images while they fit the budget,
+    else repeated samples of one image, extrapolated."""
+    if w.d * w.d * w.M <= FULL_IMAGE_EVALS:
+        dt1, _, thr, desc = oracle_full(w, 1, seed=0)
+        n = max(1, min(16, int(budget_s / max(dt1, 1e-3))))
+        secs = dt1
+        if n > 1:
+            secs, _, thr, desc = oracle_full(w, n, seed=1)
     else:
-        dt, n = dt1, n1
-    return {"value": n / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"{n} image(s) of workload {w.name} (d={w.d}, M={w.M}) through projection, "
-                      f"CTF + loss + adjoint and the full gradient, FP64 brute force, "
-                      f"{dt:.2f} s on {thr} host threads"}
+        reps, wall = [], 0.0
+        while len(reps) < 8 and wall < budget_s:
+            d, dw, thr, desc = oracle_sampled(w, seed=len(reps))
+            reps.append(d)
+            wall += dw
+        secs = sum(reps) / len(reps)
+        desc = f"{len(reps)} samples ({wall:.1f} s of host time), each " + desc + " (value extrapolated)"
+    return {"value": 1.0 / secs, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": desc + f"; {secs:.3g} s per image on {thr} host threads"}
 
 
 def run_reference(args):
-    """--impl reference: the oracle on the host cores, K steps of a bounded sample."""
+    """--impl reference: the oracle on the host cores, K steps, each a bounded
+    sample of the workload (one whole image, or one image sampled and
+    extrapolated when whole images are too costly).  ms_per_step is the
+    steps' own wall time; value is images per second of oracle work (for a
+    sampled step, the image's extrapolated cost)."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
@@ -249,20 +323,22 @@ def run_reference(args):
 
     w = syn.WORKLOADS[args.workload]
     for i in range(args.warmup):
-        oracle_sample(w, 1, seed=100 + i)
-    tot, imgs, thr = 0.0, 0, 1
+        oracle_per_image(w, seed=100 + i)
+    per_image, wall, thr, desc = 0.0, 0.0, 1, ""
     for i in range(args.steps):
-        dt, n, thr = oracle_sample(w, 1, seed=200 + i)
-        tot += dt
-        imgs += n
-    value = imgs / tot
+        dt, dw, thr, desc = oracle_per_image(w, seed=200 + i)
+        per_image += dt
+        wall += dw
+    value = args.steps / per_image
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": f"1 image of workload {w.name} per step (full M and d), FP64 oracle"},
+                         "sample": "per step: " + desc + (
+                             "" if w.d * w.d * w.M <= FULL_IMAGE_EVALS else
+                             f" (value extrapolated: {per_image / args.steps:.3g} s per image)")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -274,6 +350,127 @@ def workload_config(w):
                         f"{w.n_clusters} clusters, CTF from parameters",
             "d": w.d, "M": w.M, "global_batch": w.B, "tau": w.tau, "norm_mode": w.norm_mode,
             "zsort": 1, "l2": "flushed between timed steps (256 MB write)"}
+
+
+# ------------------------------------------------------- parity -------------
+
+def parity_check(ctx, w, D, host, dev, n_pix: int = 96, n_img: int = 2, n_sel: int = 12):
+    """Error of this workload's step against the FP64 oracle, on outputs the
+    oracle can compute one by one at full size (run after the timed region):
+      projection   n_pix sampled pixels (half near the particle) against
+                   oracle.project_pixels; tolerance 1e-5 of the image maximum
+                   plus tau for each pair float32 may decide differently
+                   (at most a few per pixel here: 8 tau);
+      ctf_loss     per-image losses of n_img images: the oracle's Eq. loss on
+                   this step's projection of those images (an oracle
+                   projection of a whole image at this size takes minutes on
+                   the host); relative tolerance 1e-5;
+      gradient     n_sel sampled Gaussians, upstream gradient = this step's
+                   dL/dI^, against oracle.grad: per Gaussian ||dg|| <= 1e-4
+                   ||g|| plus the terms of its pairs within 1e-5 relative of
+                   tau (oracle.grad_border)."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    B, d = w.B, w.d
+    proj = torch.empty(B, d, d, device=dev)
+    ctx.gem_project(D["params"], D["R"], D["t"], proj)
+    li = torch.empty(B, dtype=torch.float64, device=dev)
+    dproj = torch.empty(B, d, d, device=dev)
+    ctx.gem_ctf_loss(proj, D["images"], ctf_params=D["ctf_params"], dproj=dproj, loss_img=li)
+    grad = torch.empty(w.M, 11, device=dev)
+    ctx.gem_project_backward(dproj, grad)
+    if ctx.gem_status() != 0:
+        raise RuntimeError("device status in the parity check: " + ctx.lib.gem_last_error(ctx.h).decode())
+    P = proj.cpu().numpy()
+    rng = np.random.default_rng(2024)
+    b = rng.integers(0, B, n_pix)
+    c, r = d // 2, int(0.3 * d)
+    near = np.arange(n_pix) < n_pix // 2
+    v = np.where(near, rng.integers(c - r, c + r, n_pix), rng.integers(0, d, n_pix))
+    u = np.where(near, rng.integers(c - r, c + r, n_pix), rng.integers(0, d, n_pix))
+    pix = (b * d + v) * d + u
+    ref = oracle.project_pixels(host["params"], host["R"], host["t"], d, w.apix, w.tau, pix, w.norm_mode)
+    perr = float(np.max(np.abs(P.reshape(-1)[pix] - ref)))
+    scale = float(np.abs(P).max())
+    ptol = 1e-5 * scale + 8 * w.tau
+    imgs = np.unique(np.linspace(0, B - 1, n_img).astype(int))
+    H = oracle.ctf_grid_from_params(host["ctf_params"][imgs], d, w.apix)
+    _, _, oli, _ = oracle.loss(H, P[imgs], host["images"][imgs])
+    lerr = float(np.max(np.abs(li.cpu().numpy()[imgs] - oli) / np.abs(oli)))
+    sel = rng.choice(w.M, size=n_sel, replace=False)
+    g = dproj.cpu().numpy().astype(np.float64)
+    gref = oracle.grad(host["params"], host["R"], host["t"], d, w.apix, w.tau, g, w.norm_mode, sel=sel)
+    gb = oracle.grad_border(host["params"], host["R"], host["t"], d, w.apix, w.tau, g, 1e-5, w.norm_mode, sel=sel)
+    got = grad.cpu().numpy().astype(np.float64)[sel]
+    ratio, rel = 0.0, 0.0
+    for k in range(n_sel):
+        nrm = np.linalg.norm(gref[k])
+        err = np.linalg.norm(got[k] - gref[k])
+        if nrm > 0:
+            rel = max(rel, err / nrm)
+        bound = 1e-4 * nrm + np.linalg.norm(gb[k])
+        ratio = max(ratio, err / bound if bound > 0 else (0.0 if err == 0 else float("inf")))
+    return {
+        "oracle": "FP64 brute force on the host (every pixel against every Gaussian)",
+        "projection": {"pixels": int(n_pix), "max_abs_err": perr, "image_max": scale, "tol": ptol,
+                       "ok": bool(perr <= ptol)},
+        "ctf_loss": {"images": int(len(imgs)), "max_rel_err": lerr, "tol": 1e-5, "ok": bool(lerr <= 1e-5),
+                     "input": "this step's projection of those images"},
+        "gradient": {"gaussians": int(n_sel), "max_rel_err": float(rel), "tol": 1e-4,
+                     "max_err_over_bound": float(ratio), "ok": bool(ratio <= 1.0),
+                     "bound": "1e-4 ||g_k|| + the terms of its pairs within 1e-5 relative of tau",
+                     "upstream": "this step's dL/dI^"},
+    }
+
+
+def time_secondary(w, dev, stream, flush, steps: int, warm: int):
+    """Device time of the step on another workload (same protocol as the
+    main timed region, one GPU)."""
+    import torch
+
+    from paper_2509_25075_gb300 import binding
+    from paper_2509_25075_gb300 import synthetic as syn
+
+    host = syn.batch(w, seed=w.seed + 1000)
+    host["params"] = syn.gaussians(w)
+    D = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    ctx = binding.Context(w.d, w.apix, w.B, w.M, tau=w.tau, norm_mode=w.norm_mode, zsort=1, stream=stream)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(w.M, 11, device=dev)
+
+    def step():
+        ctx.gem_forward(D["params"], D["R"], D["t"], D["images"], loss, ctf_params=D["ctf_params"])
+        ctx.gem_backward(grad)
+
+    for _ in range(warm):
+        flush.zero_()
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ctx.gem_status() != 0:
+        raise RuntimeError("device status (secondary): " + ctx.lib.gem_last_error(ctx.h).decode())
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    ctx.gem_timing(True)
+    stage = {k: 0.0 for k in binding.STAGES}
+    n = max(1, min(steps, 10))
+    for _ in range(n):
+        flush.zero_()
+        step()
+        m, _ = ctx.gem_timing_read()
+        for k in stage:
+            stage[k] += m[k] / n
+    ctx.close()
+    return {"value": w.B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "config": workload_config(w), "stages_ms": stage, "timing": "device (CUDA events), L2 flushed"}
 
 
 # --------------------------------------------------------------- main ------
@@ -461,16 +658,24 @@ def main():
     peak = sms * per_clk * mhz * 1e6 / 1e9  # Gpair/s
     peak_sfu = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9
     achieved = kept / (per_stage[dom] / 1e3) / 1e9
-    traffic = None
-    if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] and w.name == CAPTURED_TRAFFIC["workload"]:
-        traffic = CAPTURED_TRAFFIC[dom]
+    cap = CAPTURED_TRAFFIC["per_workload"].get(w.name) \
+        if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] else None
+    traffic = cap[dom] if cap else None
     other = "raster_bwd" if dom == "raster_fwd" else "raster_fwd"
     o_peak = sms * min(FP32_PER_CLK_PER_SM / FP32_OPS_PER_KEPT_PAIR[other], EX2_PER_CLK_PER_SM) * mhz * 1e6 / 1e9
     o_ach = kept / (per_stage[other] / 1e3) / 1e9
+
+    def all_ops_peak(k):
+        return sms * min(FP32_PER_CLK_PER_SM / ALL_FP32_OPS_PER_KEPT_PAIR[k], EX2_PER_CLK_PER_SM) * mhz * 1e6 / 1e9
+
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+            "ops_per_kept_pair": FP32_OPS_PER_KEPT_PAIR[dom],
+            "frac_all_fp32_ops": achieved / all_ops_peak(dom),
             "other_rasteriser": {"kernel": other, "achieved": o_ach, "peak": o_peak, "frac": o_ach / o_peak,
-                                 "traffic": CAPTURED_TRAFFIC[other] if traffic is not None else None},
+                                 "ops_per_kept_pair": FP32_OPS_PER_KEPT_PAIR[other],
+                                 "frac_all_fp32_ops": o_ach / all_ops_peak(other),
+                                 "traffic": cap[other] if cap else None},
             "peak_note": f"{sms} SMs x min({FP32_PER_CLK_PER_SM} FP32 lanes / {ops} FMA-pipe ops per kept "
                          f"pair, {EX2_PER_CLK_PER_SM} ex2) per clock x {mhz:.0f} MHz median SM clock under load",
             "sfu_only": {"peak": peak_sfu, "frac": achieved / peak_sfu,
@@ -588,6 +793,18 @@ def main():
                  "nearest_neighbour_ms": k_ms, "nearest_neighbour_k": 1,
                  "l2": "flushed before each timed call (256 MB write)"}
 
+    # ---- error against the FP64 oracle, on sampled outputs of this step's inputs
+    parity = None
+    if rank == 0 and not args.no_parity:
+        parity = parity_check(ctx, w, D, host, dev)
+
+    # ---- other workloads, device-timed (one GPU only)
+    secondary = None
+    if ws == 1 and args.secondary:
+        secondary = {}
+        for name in [x for x in args.secondary.split(",") if x and x != w.name]:
+            secondary[name] = time_secondary(syn.WORKLOADS[name], dev, stream, flush, args.steps, warm)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w)
@@ -599,7 +816,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w), "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "plain": plain,
-            "stages_ms": per_stage, "loss": step_loss, "query": query, "train": train,
+            "stages_ms": per_stage, "loss": step_loss, "parity": parity, "secondary": secondary,
+            "query": query, "train": train,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -372,6 +372,40 @@ int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float *proj, con
                         const float *ctf_params, const float *images, float *pred,
                         float *dproj, double *loss_img, double *loss, void *cuda_stream);
 
+/* ---- rasteriser configurations and the autotuner ----------------------- */
+
+/* Both rasterisers come in several kernel configurations that compute the
+ * same result (bitwise, for a given configuration; within float rounding
+ * across configurations): the forward (step a3) as equal runs of items
+ * across blocks or runs aligned to blocks, with 256- or 512-record windows,
+ * a per-tile grid or a persistent grid that takes tiles longest-first from
+ * a counter; the backward (a5) with 1, 2 or 4 lanes per record.  Which is
+ * fastest depends on the image side, the batch and the Gaussians' sizes.
+ * Counts of each kind (kind 0: forward, 1: backward); a configuration's
+ * description ("" if out of range). */
+int gem_raster_config_count(int32_t *n_fwd, int32_t *n_bwd);
+const char *gem_raster_config_name(int32_t kind, int32_t i);
+
+/* Use configurations fwd, bwd (indices; -1 for either: the autotuner's
+ * choice for the call's shape, else the library default).  Errors:
+ * GEM_EINVAL (index out of range). */
+int gem_set_raster_config(gem_ctx *ctx, int32_t fwd, int32_t bwd);
+
+/* The configurations a call with B images and M Gaussians would use. */
+int gem_get_raster_config(const gem_ctx *ctx, int32_t B, int64_t M, int32_t *fwd, int32_t *bwd);
+
+/* Autotuner: project params, R, t (as gem_project) once, then time every
+ * forward configuration and every backward configuration reps times each
+ * (after one warm-up launch) on these bins with CUDA events, and record the
+ * fastest of each for this shape (device, d, B, bit length of M) in a
+ * process-wide table that every context consults when its configuration is
+ * -1 (the default).  Writes the choices to *fwd, *bwd (either may be NULL).
+ * Synchronises the stream (not capturable); the first call allocates
+ * max_M x 11 floats of scratch that the context keeps; ends the state kept
+ * for gem_backward.  Errors: as gem_project, GEM_ENOMEM, GEM_ECUDA. */
+int gem_autotune(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
+                 const float *t, int32_t reps, int32_t *fwd, int32_t *bwd);
+
 /* ---- per-stage timing ---------------------------------------------------- */
 
 /* Stages of the hot path, as timed by gem_timing_read. */

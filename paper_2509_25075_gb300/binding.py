@@ -84,6 +84,11 @@ SIGNATURES = {
     "gem_inspect_bins": (ctypes.c_int, [_P, _P, _P, _I64]),
     "gem_inspect_records": (ctypes.c_int, [_P, _P]),
     "gem_pair_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "gem_raster_config_count": (ctypes.c_int, [ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "gem_raster_config_name": (ctypes.c_char_p, [_I32, _I32]),
+    "gem_set_raster_config": (ctypes.c_int, [_P, _I32, _I32]),
+    "gem_get_raster_config": (ctypes.c_int, [_P, _I32, _I64, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "gem_autotune": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "gem_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "gem_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "gem_ctf_loss_static": (ctypes.c_int, [_I32, _F, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -143,6 +148,15 @@ def _check(x, name, shape, dtype=torch.float32, optional=False):
         raise ValueError(f"{name} must be contiguous")
     if shape is not None and tuple(x.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+
+
+def raster_configs():
+    """-> (forward configuration names, backward configuration names)."""
+    lib = load()
+    nf, nb = ctypes.c_int32(), ctypes.c_int32()
+    lib.gem_raster_config_count(ctypes.byref(nf), ctypes.byref(nb))
+    return ([lib.gem_raster_config_name(0, i).decode() for i in range(nf.value)],
+            [lib.gem_raster_config_name(1, i).decode() for i in range(nb.value)])
 
 
 class Context:
@@ -385,6 +399,28 @@ class Context:
         _check(idx, "idx", (M, k), torch.int32)
         self._rc(self.lib.gem_nn_distance(self.h, _ptr(params), M, k, _ptr(dist), _ptr(idx)))
         return dist, idx
+
+    # -- rasteriser configurations and the autotuner ---------------------------
+    def raster_configs(self):
+        return raster_configs()
+
+    def gem_set_raster_config(self, fwd: int = -1, bwd: int = -1):
+        self._rc(self.lib.gem_set_raster_config(self.h, fwd, bwd))
+
+    def gem_get_raster_config(self, B: int, M: int):
+        f, b = ctypes.c_int32(), ctypes.c_int32()
+        self._rc(self.lib.gem_get_raster_config(self.h, B, M, ctypes.byref(f), ctypes.byref(b)))
+        return f.value, b.value
+
+    def gem_autotune(self, params, R, t, reps: int = 3):
+        """Time every rasteriser configuration on this shape; the fastest pair
+        is recorded for the process.  -> (forward index, backward index)."""
+        M, B = self._views(params, R, t)
+        f, b = ctypes.c_int32(), ctypes.c_int32()
+        self._rc(self.lib.gem_autotune(self.h, _ptr(params), M, B, _ptr(R), _ptr(t), reps,
+                                       ctypes.byref(f), ctypes.byref(b)))
+        self.M = self.B = None
+        return f.value, b.value
 
     def gem_timing(self, enable: bool):
         self._rc(self.lib.gem_timing(self.h, 1 if enable else 0))

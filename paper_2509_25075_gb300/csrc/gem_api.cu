@@ -9,7 +9,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "gem.h"
@@ -65,6 +68,13 @@ struct gem_ctx {
   // Gaussians given by gem_set_gaussians (used by gem_forward with params = NULL)
   const float *set_params = nullptr;
   int64_t set_M = 0;
+  // rasteriser kernel configurations (indices into the tables of
+  // gem_raster.cu); -1: the autotuner's cached choice for the call's shape,
+  // else the default
+  int fwd_cfg = -1, bwd_cfg = -1;
+  uint32_t *order = nullptr;     // [max_B * T] tile order of the persistent forward
+  unsigned *next_tile = nullptr;  // [1] its work counter
+  float *tune_grad = nullptr;     // [max_M][11] gradient the autotuner's backward writes
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
   bool timing = false;
@@ -88,6 +98,35 @@ struct gem_ctx {
   int64_t M = 0;
   int B = 0;
 };
+
+// The configurations used when neither the context nor the autotuner's cache
+// names one (the fastest measured on the benchmark workloads).
+constexpr int kDefaultFwdCfg = 0;
+constexpr int kDefaultBwdCfg = 0;
+
+// The autotuner's choices, shared by every context of the process: keyed by
+// device, image side, batch and the bit length of M (shapes that bin alike).
+namespace {
+struct TuneKey {
+  int dev, d, B, mbits;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, d, B, mbits) < std::tie(o.dev, o.d, o.B, o.mbits);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+
+TuneKey tune_key(int d, int B, int64_t M) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int bits = 0;
+  while (bits < 63 && ((int64_t)1 << bits) <= M) ++bits;
+  return TuneKey{dev, d, B, bits};
+}
+}  // namespace
+
+static int active_fwd(const gem_ctx *c, int B, int64_t M);
+static int active_bwd(const gem_ctx *c, int B, int64_t M);
 
 static int fail(gem_ctx *c, int code, const char *fmt, ...) {
   if (c) {
@@ -236,7 +275,8 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->dproj, (size_t)g.max_B * d * d) &&
             alloc(c, &c->Z, (size_t)g.max_B * d * d) && alloc(c, &c->tw, (size_t)d) &&
             alloc(c, &c->lossp, (size_t)g.max_B * (ctf_partials(d) + 1)) && alloc(c, &c->status, 1) &&
-            alloc(c, &c->kept, 2);
+            alloc(c, &c->kept, 2) &&
+            alloc(c, &c->order, (size_t)g.max_B * c->T) && alloc(c, &c->next_tile, 1);
   // nearest-neighbour grid: at most 2 max_M + 64 cells
   c->knn.cap = 2 * g.max_M + 64;
   ok = ok && alloc(c, &c->knn.part, 608 * 6) && alloc(c, &c->knn.grid, 1) &&
@@ -372,8 +412,9 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   }
   {
     StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
-    if ((e = launch_raster_fwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, M, B, g.d,
-                               c->l2tau, proj, c->stream)) != cudaSuccess)
+    if ((e = launch_raster_fwd(active_fwd(c, B, M), c->rec, c->bin.list, c->bin.lmask,
+                               c->bin.tile_start, c->bin.cap, M, B, g.d, c->l2tau, proj, c->order,
+                               c->next_tile, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "raster_fwd");
   }
   c->have_proj = true;
@@ -434,8 +475,9 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     if (dense)
       e = launch_dense_bwd(c->rec, c->M, c->B, g.d, c->l2tau, dproj, c->mom, c->stream);
     else
-      e = launch_raster_bwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, c->M, c->B,
-                            g.d, c->l2tau, dproj, c->mom, c->stream);
+      e = launch_raster_bwd(active_bwd(c, c->B, c->M), c->rec, c->bin.list, c->bin.lmask,
+                            c->bin.tile_start, c->bin.cap, c->M, c->B, g.d, c->l2tau, dproj, c->mom,
+                            c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
   StageScope sc(c, GEM_STAGE_PREP_BWD, 2);
@@ -582,8 +624,9 @@ int gem_pair_stats(gem_ctx *c, int64_t *kept, int64_t *evaluated) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(c->kept, 0, 2 * sizeof(unsigned long long), c->stream)) !=
           cudaSuccess ||
-      (e = launch_count_kept(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap,
-                             c->bins_M, c->bins_B, g.d, c->bins_l2tau, c->kept, c->stream)) !=
+      (e = launch_count_kept(active_fwd(c, c->bins_B, c->bins_M), c->rec, c->bin.list,
+                             c->bin.lmask, c->bin.tile_start, c->bin.cap, c->bins_M, c->bins_B, g.d,
+                             c->bins_l2tau, c->kept, c->order, c->next_tile, c->stream)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "pair count");
@@ -654,8 +697,9 @@ int gem_query(gem_ctx *c, const float *params, int64_t M, float tau, float *vol)
             cudaSuccess ||
         (e = launch_bin(c->rec, c->bin.key, M, ns, g.d, l2tau, 0, c->bin, &perm, c->stream)) !=
             cudaSuccess ||
-        (e = launch_raster_fwd(c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap,
-                               M, ns, g.d, l2tau, vol + (size_t)k0 * slice, c->stream)) !=
+        (e = launch_raster_fwd(active_fwd(c, ns, M), c->rec, c->bin.list, c->bin.lmask,
+                               c->bin.tile_start, c->bin.cap, M, ns, g.d, l2tau,
+                               vol + (size_t)k0 * slice, c->order, c->next_tile, c->stream)) !=
             cudaSuccess)
       return cuda_fail(c, e, "query");
     c->have_bins = true;
@@ -810,4 +854,124 @@ int gem_nn_distance(gem_ctx *c, const float *params, int64_t M, int32_t k, float
   return GEM_OK;
 }
 
+int gem_raster_config_count(int32_t *n_fwd, int32_t *n_bwd) {
+  if (n_fwd) *n_fwd = fwd_config_count();
+  if (n_bwd) *n_bwd = bwd_config_count();
+  return GEM_OK;
+}
+
+const char *gem_raster_config_name(int32_t kind, int32_t i) {
+  if (kind == 0 && i >= 0 && i < fwd_config_count()) return fwd_config(i).name;
+  if (kind == 1 && i >= 0 && i < bwd_config_count()) return bwd_config(i).name;
+  return "";
+}
+
+int gem_set_raster_config(gem_ctx *c, int32_t fwd, int32_t bwd) {
+  if (!c) return GEM_EINVAL;
+  if (fwd < -1 || fwd >= fwd_config_count() || bwd < -1 || bwd >= bwd_config_count())
+    return fail(c, GEM_EINVAL, "raster config (%d, %d) outside -1..(%d, %d)", fwd, bwd,
+                fwd_config_count() - 1, bwd_config_count() - 1);
+  c->fwd_cfg = fwd;
+  c->bwd_cfg = bwd;
+  return GEM_OK;
+}
+
+int gem_get_raster_config(const gem_ctx *c, int32_t B, int64_t M, int32_t *fwd, int32_t *bwd) {
+  if (!c || !fwd || !bwd) return GEM_EINVAL;
+  *fwd = active_fwd(c, B, M);
+  *bwd = active_bwd(c, B, M);
+  return GEM_OK;
+}
+
+int gem_autotune(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
+                 const float *t, int32_t reps, int32_t *fwd_out, int32_t *bwd_out) {
+  if (!c) return GEM_EINVAL;
+  if (reps < 1 || reps > 1000) return fail(c, GEM_EINVAL, "reps=%d outside 1..1000", reps);
+  int rc = check_project_args(c, params, M, B, R, t, c->proj);
+  if (rc) return rc;
+  const gem_config &g = c->cfg;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(c, e, "autotune events");
+  }
+  if (!c->tune_grad && !alloc(c, &c->tune_grad, (size_t)g.max_M * kNpar)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(c, GEM_ENOMEM, "autotune scratch allocation failed");
+  }
+  const int keep_f = c->fwd_cfg, keep_b = c->bwd_cfg;
+  const bool keep_timing = c->timing;
+  c->timing = false;
+  // bins of this shape, then each forward configuration on them
+  c->fwd_cfg = kDefaultFwdCfg;
+  c->bwd_cfg = kDefaultBwdCfg;
+  rc = gem_project(c, params, M, B, R, t, c->proj);
+  float best_f = INFINITY, best_b = INFINITY;
+  int bf = kDefaultFwdCfg, bb = kDefaultBwdCfg;
+  for (int i = 0; rc == GEM_OK && i < fwd_config_count(); ++i) {
+    float ms = 0.f;
+    for (int r = -1; r < reps; ++r) {  // r = -1: warm-up
+      cudaEventRecord(e0, c->stream);
+      e = launch_raster_fwd(i, c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, M,
+                            B, g.d, c->l2tau, c->proj, c->order, c->next_tile, c->stream);
+      cudaEventRecord(e1, c->stream);
+      if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+        rc = cuda_fail(c, e, "autotune forward");
+        break;
+      }
+      float x = 0.f;
+      cudaEventElapsedTime(&x, e0, e1);
+      if (r >= 0) ms += x;
+    }
+    if (rc == GEM_OK && ms < best_f) best_f = ms, bf = i;
+  }
+  // each backward configuration, upstream gradient = the projection (the
+  // cost does not depend on its values), moments cleared by the chain rule
+  for (int i = 0; rc == GEM_OK && i < bwd_config_count(); ++i) {
+    c->bwd_cfg = i;
+    float ms = 0.f;
+    for (int r = -1; r < reps && rc == GEM_OK; ++r) {
+      cudaEventRecord(e0, c->stream);
+      rc = backward_common(c, c->proj, c->tune_grad, false);
+      cudaEventRecord(e1, c->stream);
+      if (rc == GEM_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(c, e, "autotune backward");
+      float x = 0.f;
+      if (rc == GEM_OK) cudaEventElapsedTime(&x, e0, e1);
+      if (r >= 0) ms += x;
+    }
+    if (rc == GEM_OK && ms < best_b) best_b = ms, bb = i;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = keep_timing;
+  c->fwd_cfg = keep_f;
+  c->bwd_cfg = keep_b;
+  c->have_proj = false;  // the autotuner's projection is not the caller's
+  c->have_dproj = false;
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[tune_key(g.d, B, M)] = std::make_pair(bf, bb);
+  }
+  if (fwd_out) *fwd_out = bf;
+  if (bwd_out) *bwd_out = bb;
+  return GEM_OK;
+}
+
 }  // extern "C"
+
+static int active_fwd(const gem_ctx *c, int B, int64_t M) {
+  if (c->fwd_cfg >= 0) return c->fwd_cfg;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(c->cfg.d, B, M));
+  return it == g_tune.end() ? kDefaultFwdCfg : it->second.first;
+}
+
+static int active_bwd(const gem_ctx *c, int B, int64_t M) {
+  if (c->bwd_cfg >= 0) return c->bwd_cfg;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(c->cfg.d, B, M));
+  return it == g_tune.end() ? kDefaultBwdCfg : it->second.second;
+}

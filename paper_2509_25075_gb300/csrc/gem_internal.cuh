@@ -64,45 +64,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// (s, c) += x componentwise, compensated (Kahan): the sum is s - c.  Every
-// step is an explicit rounded operation, so no contraction can change it.
-__device__ __forceinline__ void kahan2(float2 &s, float2 &c, float2 x) {
-  const float2 n1 = make_float2(-1.f, -1.f);
-  const float2 y = fma2(c, n1, x);  // x - c
-  const float2 t = add2(s, y);
-  c = fma2(y, n1, fma2(s, n1, t));  // (t - s) - y
-  s = t;
-}
-
-// float32 <-> float64 by rewriting the IEEE 754 fields with integer
-// operations: GB300's FP64 pipe is a small fraction of its FP32 rate, and
-// the moments only need their bits moved.  float -> double is exact (zero
-// and subnormal floats become a signed zero; infinities and NaN keep their
-// class).  double -> float rounds half away from zero on the 29 dropped
-// mantissa bits (a carry into the exponent is the correct result); results
-// below the float normal range flush to a signed zero, above it become
-// infinity.
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned sign = u & 0x80000000u;
-  unsigned hi = sign | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-  unsigned lo = u << 29;
-  if (e == 0u) hi = sign, lo = 0u;
-  if (e == 0xffu) hi = sign | 0x7ff00000u | ((u >> 3) & 0xfffffu);
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ float f64_to_f32(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u | (e == 1151 && ((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
-  if (e <= 0) return __uint_as_float(sign);
-  const unsigned mag = ((unsigned)e << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
-  return __uint_as_float(sign | mag);
-}
-
 // Rotation matrix of a unit quaternion (w, x, y, z), entry formula.
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
   R[0] = 1.f - 2.f * (y * y + z * z);
@@ -300,15 +261,36 @@ size_t bin_chunks_tiles(int64_t M);
 cudaError_t bin_configure(int d);
 
 // gem_raster.cu
-cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+// A configuration of the forward rasteriser: form 0 = equal runs across
+// blocks, 1 = block-aligned runs; sub = 128-record sub-windows per window;
+// minb = CTAs per SM the launch bound asks for; persistent = a grid of
+// minb CTAs per SM pulling tiles longest-first from a counter.
+struct FwdCfg {
+  int form, sub, minb, persistent;
+  const char *name;
+};
+int fwd_config_count();
+const FwdCfg &fwd_config(int i);
+// order [B*T] and next_tile [1] are scratch of the persistent forms.
+cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, float *proj, cudaStream_t st);
-cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+                              float l2tau, float *proj, uint32_t *order, unsigned *next_tile,
+                              cudaStream_t st);
+// A configuration of the backward rasteriser: lanes sharing one record,
+// records per lane per warp window.
+struct BwdCfg {
+  int lanes, per;
+  const char *name;
+};
+int bwd_config_count();
+const BwdCfg &bwd_config(int i);
+cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, cudaStream_t st);
-cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
-                              const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, unsigned long long *kept, cudaStream_t st);
+cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
+                              const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+                              int64_t M, int B, int d, float l2tau, unsigned long long *kept,
+                              uint32_t *order, unsigned *next_tile, cudaStream_t st);
 cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2tau, float *proj,
                              cudaStream_t st);
 cudaError_t launch_dense_bwd(const Rec *rec, int64_t M, int B, int d, float l2tau,

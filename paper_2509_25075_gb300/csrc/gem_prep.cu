@@ -237,9 +237,9 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
     if ((ma.x | ma.y | mb.x | mb.y | mc.x | mc.y) == 0) continue;
     // leave the moments cleared for the next backward pass
     mm[0] = mm[1] = mm[2] = make_longlong2(0, 0);
-    const float m0 = f64_to_f32(__longlong_as_double(ma.x)), m1 = f64_to_f32(__longlong_as_double(ma.y));
-    const float m2 = f64_to_f32(__longlong_as_double(mb.x)), m3 = f64_to_f32(__longlong_as_double(mb.y));
-    const float m4 = f64_to_f32(__longlong_as_double(mc.x)), m5 = f64_to_f32(__longlong_as_double(mc.y));
+    const float m0 = (float)__longlong_as_double(ma.x), m1 = (float)__longlong_as_double(ma.y);
+    const float m2 = (float)__longlong_as_double(mb.x), m3 = (float)__longlong_as_double(mb.y);
+    const float m4 = (float)__longlong_as_double(mc.x), m5 = (float)__longlong_as_double(mc.y);
     float Rl[9], tl[2];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);

@@ -29,11 +29,13 @@
 //     for a wide Gaussian under a smooth upstream gradient the conic and
 //     amplitude terms of dL/dS^ nearly cancel, and this form lets that
 //     cancellation happen inside an accurate sum instead of in the float32
-//     chain rule.  Each block's sums join the lane's totals with Kahan
-//     compensation; the two lanes add their halves, and the (tile, Gaussian)
-//     partial goes to float64 moments in global memory (L2 atomics), so the
-//     sum over a Gaussian's tiles is exact to float64.  No barrier couples
+//     chain rule.  Each block's sums join the lane's totals; the two lanes
+//     add their halves, and the (tile, Gaussian) partial goes to float64
+//     moments in global memory (L2 atomics), so the sum over a Gaussian's
+//     tiles loses nothing to rounding.  No barrier couples
 //     the warps.  a6 turns the moments into parameter gradients.
+#include <type_traits>
+
 #include "gem_internal.cuh"
 
 namespace gem {
@@ -50,8 +52,6 @@ constexpr int kSub = 2;                // forward: records staged per thread per
 constexpr int kWin = kThreads * kSub;  // records staged per window
 static_assert(kThreads == 128, "the forward splits items with shifts by 7");
 constexpr int kFwdMinBlocks = 9;      // forward: CTAs per SM (10, with fewer registers, ran slower)
-constexpr int kBwdLanes = 2;          // backward: lanes sharing one record
-constexpr int kBwdPer = 4;            // backward: records per lane per warp window
 
 // kCount = true: the same walk, counting kept pairs into kept[0] and
 // evaluated pairs into kept[1] instead of writing the projection
@@ -257,24 +257,342 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
       make_float2(own0.x - own0.y, own1.x - own1.y);
 }
 
-cudaError_t launch_raster_fwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
-                              const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, float *proj, cudaStream_t st) {
-  int nt = d / kTile;
-  dim3 grid(nt * nt, B);
-  raster_fwd_kernel<false><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                      l2tau, proj, nullptr);
+// a3, block-aligned form.  The window's (block, record) items are laid out
+// block after block as above, but the 128 threads are shared among the
+// blocks in proportion to their item counts (every non-empty block gets at
+// least one thread: thread range [T_k, T_k+1) with T_k = (non-empty blocks
+// before k) + floor((128 - non-empty) * start_k / N)), and a block's threads
+// split its items evenly.  A run never leaves its block, so each thread ends
+// the window with one partial image of its block (16 pixels), and each pixel
+// sums the partials of its block's thread range in thread order (runs in
+// list order), then joins its running sum with Kahan compensation.  The
+// longest run is within 128 / (128 - 16) of the mean.  kSub sub-windows of
+// 128 records make a window; flat slots are bytes up to 256 records.
+template <int kSubW>
+struct FlatSlot {
+  using T = typename std::conditional<(kSubW * 128 <= 256), unsigned char, unsigned short>::type;
+};
+
+template <int kSubW, int kMinB, bool kCount>
+__global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
+    const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
+    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    int64_t M, int d, float l2tau, const uint32_t *__restrict__ order, int ntiles,
+    unsigned *__restrict__ next_tile, float *__restrict__ proj,
+    unsigned long long *__restrict__ kept) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kWinW = kThreads * kSubW;
+  using Slot = typename FlatSlot<kSubW>::T;
+  __shared__ float4 sa[kWinW];                        // px, py, ca, cb
+  __shared__ float2 sb[kWinW];                        // cc, log2 A
+  __shared__ Slot flat[16 * kWinW];                   // staged slot of each (block, record) item
+  __shared__ unsigned short wcnt[kSubW][kWarps][16];  // per sub-window, warp, block: how many
+  __shared__ unsigned wbal[kSubW][kWarps][16];        // per sub-window, warp, block: which lanes
+  __shared__ int woff[kWarps][kSubW][16];             // where a warp's records go in flat
+  __shared__ int pstart[kWarps][17];                  // block k's items: [pstart[k], pstart[k+1])
+  __shared__ int tfirst[kWarps][17];                  // block k's threads: [tfirst[k], tfirst[k+1])
+  __shared__ float4 part[kThreads][4];                // each thread's partial image of its block
+  __shared__ int tile_sh;
+  const int nt = d / kTile, T = nt * nt;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // pixels owned across windows: two columns of one row of block ob
+  const int ob = tid >> 3, ow = tid & 7;
+  unsigned nkept = 0, neval = 0;
+  // tiles come from the grid (order == nullptr) or, in the persistent form,
+  // from a shared counter over a longest-first order
+  for (int it = 0;; ++it) {
+    int bt;
+    if (order == nullptr) {
+      if (it > 0) break;
+      bt = blockIdx.y * T + blockIdx.x;
+    } else {
+      __syncthreads();  // every thread has read the previous tile_sh
+      if (tid == 0) tile_sh = (int)atomicAdd(next_tile, 1u);
+      __syncthreads();
+      const int q = tile_sh;
+      if (q >= ntiles) break;
+      bt = (int)order[q];
+    }
+    const int b = bt / T, t = bt - b * T;
+    const int tx = t % nt, ty = t / nt;
+    const int x0 = tx * kTile, y0 = ty * kTile;
+    int64_t s = tile_start[bt];
+    int64_t e = tile_start[bt + 1];
+    e = min(e, cap);
+    s = min(s, e);
+    const Rec *rb = rec + (int64_t)b * M;
+    float2 own0 = make_float2(0.f, 0.f), own1 = make_float2(0.f, 0.f);  // Kahan (sum, comp)
+    for (int64_t base = s; base < e; base += kWinW) {
+      const int n = (int)min((int64_t)kWinW, e - base);
+      __syncthreads();  // previous window fully consumed
+      unsigned m[kSubW];
+#pragma unroll
+      for (int u = 0; u < kSubW; ++u) {
+        const int slot = u * kThreads + tid;
+        m[u] = 0;
+        if (slot < n) {
+          const Rec *rp = rb + list[base + slot];
+          const float4 ra = rp->a;
+          const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
+          m[u] = lmask[base + slot];
+          sa[slot] = ra;
+          sb[slot] = rbv;
+        }
+        unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const unsigned bk = __ballot_sync(0xffffffffu, (m[u] >> k) & 1u);
+          if (lane == k) mybal = bk;
+        }
+        if (lane < 16) {
+          wcnt[u][warp][lane] = (unsigned short)__popc(mybal);
+          wbal[u][warp][lane] = mybal;
+        }
+      }
+      __syncthreads();
+      // every warp: block lengths, their prefix, where its own records go,
+      // and the thread ranges of the blocks
+      {
+        int len = 0, wo[kSubW];
+#pragma unroll
+        for (int u = 0; u < kSubW; ++u) {
+          wo[u] = 0;
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) {
+            if (w == warp) wo[u] = len;
+            if (lane < 16) len += wcnt[u][w][lane];
+          }
+        }
+        int incl = len, ne = (lane < 16 && len > 0) ? 1 : 0;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          const int c = __shfl_up_sync(0xffffffffu, ne, o);
+          if (lane >= o) {
+            incl += v;
+            ne += c;
+          }
+        }
+        const int N = __shfl_sync(0xffffffffu, incl, 15);
+        const int nne = __shfl_sync(0xffffffffu, ne, 15);
+        if (lane < 16) {
+          const int st = incl - len;
+          pstart[warp][lane] = st;
+#pragma unroll
+          for (int u = 0; u < kSubW; ++u) woff[warp][u][lane] = st + wo[u];
+          // non-empty blocks before this one, plus its share of the rest
+          const int neb = ne - ((len > 0) ? 1 : 0);
+          tfirst[warp][lane] = neb + (N > 0 ? ((kThreads - nne) * st) / N : 0);
+        }
+        if (lane == 15) {
+          pstart[warp][16] = incl;
+          tfirst[warp][16] = kThreads;
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int u = 0; u < kSubW; ++u) {
+        for (unsigned mm = m[u]; mm; mm &= mm - 1) {
+          const int k = __ffs(mm) - 1;
+          flat[woff[warp][u][k] + __popc(wbal[u][warp][k] & lt)] = (Slot)(u * kThreads + tid);
+        }
+      }
+      __syncthreads();
+      // this thread's block and its share of the block's items
+      const int *ps = pstart[warp];
+      const int *tf = tfirst[warp];
+      int k = 0;
+#pragma unroll
+      for (int q = 8; q >= 1; q >>= 1)
+        if (k + q <= 15 && tf[k + q] <= tid) k += q;
+      // tf is non-decreasing and tf[16] = 128 > tid: k is the last block
+      // whose range starts at or before tid; an empty block's range is empty
+      const int t0 = tf[k], tk = tf[k + 1] - t0;
+      float2 acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+      if (tk > 0 && tid < tf[k + 1]) {
+        const int L = ps[k + 1] - ps[k], j = tid - t0;
+        const int lo = ps[k] + (j * L) / tk, hi = ps[k] + ((j + 1) * L) / tk;
+        const float X0 = (float)(x0 + 4 * (k & 3)), Y0 = (float)(y0 + 4 * (k >> 2));
+        const float2 xs01 = make_float2(X0, X0 + 1.f), xs23 = make_float2(X0 + 2.f, X0 + 3.f);
+        for (int i = lo; i < hi; ++i) {
+          const int slot = flat[i];
+          const float4 A = sa[slot];
+          const float2 Bv = sb[slot];
+          const float2 npx = f2(-A.x);
+          const float2 dx01 = add2(xs01, npx);
+          const float2 dx23 = add2(xs23, npx);
+          const float2 ca = f2(A.z);
+          const float2 cadx01 = mul2(ca, dx01), cadx23 = mul2(ca, dx23);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
+            const float dy = Y0 + (float)r - A.y;
+            const float2 bdy = f2(A.w * dy);
+            const float2 cdy = f2(fmaf(Bv.x * dy, dy, Bv.y));
+            const float2 e01 = fma2(add2(cadx01, bdy), dx01, cdy);
+            const float2 e23 = fma2(add2(cadx23, bdy), dx23, cdy);
+            if (kCount) {
+              nkept += (e01.x > l2tau) + (e01.y > l2tau) + (e23.x > l2tau) + (e23.y > l2tau);
+            } else {
+              // value on kept pairs (value > tau), zero elsewhere
+              acc[2 * r] = fma2(make_float2(ex2_approx(e01.x), ex2_approx(e01.y)),
+                                make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)), acc[2 * r]);
+              acc[2 * r + 1] =
+                  fma2(make_float2(ex2_approx(e23.x), ex2_approx(e23.y)),
+                       make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)), acc[2 * r + 1]);
+            }
+          }
+          if (kCount) neval += 16;
+        }
+      }
+      if (!kCount) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          part[tid][r] = make_float4(acc[2 * r].x, acc[2 * r].y, acc[2 * r + 1].x, acc[2 * r + 1].y);
+        __syncthreads();
+        // each owned pixel sums its block's partials in thread order (runs
+        // in list order), then joins its running sum (Kahan)
+        const int u0 = tf[ob], u1 = tf[ob + 1];
+        float2 w = make_float2(0.f, 0.f);
+        for (int u = u0; u < u1; ++u) {
+          const float2 v = reinterpret_cast<const float2 *>(&part[u][ow >> 1])[ow & 1];
+          w.x += v.x;
+          w.y += v.y;
+        }
+        if (u1 > u0) {
+          own0 = kahan_add(own0, w.x);
+          own1 = kahan_add(own1, w.y);
+        }
+      }
+    }
+    if (!kCount) {
+      const int px = x0 + 4 * (ob & 3) + 2 * (ow & 1), py = y0 + 4 * (ob >> 2) + (ow >> 1);
+      *reinterpret_cast<float2 *>(proj + ((int64_t)b * d + py) * d + px) =
+          make_float2(own0.x - own0.y, own1.x - own1.y);
+    }
+  }
+  if (kCount) {
+    for (int o = 16; o > 0; o >>= 1) {
+      nkept += __shfl_xor_sync(0xffffffffu, nkept, o);
+      neval += __shfl_xor_sync(0xffffffffu, neval, o);
+    }
+    if (lane == 0) {
+      atomicAdd(kept, (unsigned long long)nkept);
+      atomicAdd(kept + 1, (unsigned long long)neval);
+    }
+  }
+}
+
+// Longest-first order of the B*T tiles for the persistent form: a counting
+// sort of the tiles by the bit length of their list length (one CTA; 32
+// classes, longest class first, ties in any order) and the work counter
+// reset.  Which tile runs when changes nothing in its result.
+__global__ void __launch_bounds__(1024) tile_order_kernel(const int64_t *__restrict__ tile_start,
+                                                         int ntiles, uint32_t *__restrict__ order,
+                                                         unsigned *__restrict__ next_tile) {
+  __shared__ unsigned hist[32], cur[32];
+  if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+    const int64_t len = tile_start[i + 1] - tile_start[i];
+    const int c = 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
+    atomicAdd(&hist[c], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int c = 0; c < 32; ++c) {
+      cur[c] = run;
+      run += hist[c];
+    }
+    *next_tile = 0u;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
+    const int64_t len = tile_start[i + 1] - tile_start[i];
+    const int c = 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
+    order[atomicAdd(&cur[c], 1u)] = (uint32_t)i;
+  }
+}
+
+// The forward's kernel configurations (the autotuner's search space).
+static const FwdCfg kFwdCfgs[] = {
+    {0, 2, 9, 0, "runs, 256-record windows, 9 CTAs/SM"},
+    {1, 2, 9, 0, "aligned, 256-record windows, 9 CTAs/SM"},
+    {1, 2, 8, 0, "aligned, 256-record windows, 8 CTAs/SM"},
+    {1, 4, 5, 0, "aligned, 512-record windows, 5 CTAs/SM"},
+    {1, 2, 9, 1, "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first"},
+    {1, 4, 5, 1, "aligned, 512-record windows, 5 CTAs/SM, persistent longest-first"},
+};
+int fwd_config_count() { return (int)(sizeof(kFwdCfgs) / sizeof(kFwdCfgs[0])); }
+const FwdCfg &fwd_config(int i) { return kFwdCfgs[i]; }
+
+template <int kSubW, int kMinB, bool kCount>
+static cudaError_t launch_aligned(const FwdCfg &c, const Rec *rec, const uint32_t *list,
+                                  const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+                                  int64_t M, int B, int d, float l2tau, float *proj,
+                                  unsigned long long *kept, uint32_t *order, unsigned *next_tile,
+                                  cudaStream_t st) {
+  const int nt = d / kTile, ntiles = nt * nt * B;
+  if (c.persistent) {
+    tile_order_kernel<<<1, 1024, 0, st>>>(tile_start, ntiles, order, next_tile);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = max(1, min(ntiles, sms * kMinB));
+    raster_fwd_aligned_kernel<kSubW, kMinB, kCount><<<grid, kThreads, 0, st>>>(
+        rec, list, lmask, tile_start, cap, M, d, l2tau, order, ntiles, next_tile, proj, kept);
+  } else {
+    dim3 grid(nt * nt, B);
+    raster_fwd_aligned_kernel<kSubW, kMinB, kCount><<<grid, kThreads, 0, st>>>(
+        rec, list, lmask, tile_start, cap, M, d, l2tau, nullptr, 0, nullptr, proj, kept);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_count_kept(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+template <bool kCount>
+static cudaError_t launch_fwd_any(int cfg, const Rec *rec, const uint32_t *list,
+                                  const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+                                  int64_t M, int B, int d, float l2tau, float *proj,
+                                  unsigned long long *kept, uint32_t *order, unsigned *next_tile,
+                                  cudaStream_t st) {
+  if (cfg < 0 || cfg >= fwd_config_count()) return cudaErrorInvalidValue;
+  const FwdCfg &c = kFwdCfgs[cfg];
+  if (c.persistent && (order == nullptr || next_tile == nullptr)) return cudaErrorInvalidValue;
+  if (c.form == 0) {
+    const int nt = d / kTile;
+    dim3 grid(nt * nt, B);
+    raster_fwd_kernel<kCount><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                         l2tau, proj, kept);
+    return cudaGetLastError();
+  }
+  if (c.sub == 2 && c.minb == 9)
+    return launch_aligned<2, 9, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+                                        kept, order, next_tile, st);
+  if (c.sub == 2 && c.minb == 8)
+    return launch_aligned<2, 8, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+                                        kept, order, next_tile, st);
+  return launch_aligned<4, 5, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+                                      kept, order, next_tile, st);
+}
+
+cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, unsigned long long *kept, cudaStream_t st) {
-  int nt = d / kTile;
-  dim3 grid(nt * nt, B);
-  raster_fwd_kernel<true><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                     l2tau, nullptr, kept);
-  return cudaGetLastError();
+                              float l2tau, float *proj, uint32_t *order, unsigned *next_tile,
+                              cudaStream_t st) {
+  return launch_fwd_any<false>(cfg, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+                               nullptr, order, next_tile, st);
+}
+
+cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
+                              const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+                              int64_t M, int B, int d, float l2tau, unsigned long long *kept,
+                              uint32_t *order, unsigned *next_tile, cudaStream_t st) {
+  return launch_fwd_any<true>(cfg, rec, list, lmask, tile_start, cap, M, B, d, l2tau, nullptr,
+                              kept, order, next_tile, st);
 }
 
 // kLpr lanes share one record (lane q of the group takes pixel rows
@@ -384,8 +702,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       const float cb2 = cb * cb, cb2l = fmaf(cb, cb, -cb2);
       const float rD = kLog2e / (fmaf(4.f * A.z, cc, -cb2) - cb2l);
       const float sxx = -2.f * cc * rD, sxy = cb * rD, syy = -2.f * A.z * rD;
-      float2 s01 = make_float2(0.f, 0.f), s23 = s01, s45 = s01;  // Kahan sums: (n0, n1), (n2, n3), (n4, n5)
-      float2 c01 = s01, c23 = s01, c45 = s01;                    // and their compensations
+      float2 s01 = make_float2(0.f, 0.f), s23 = s01, s45 = s01;  // lane totals: (n0, n1), (n2, n3), (n4, n5)
       for (unsigned mm = mk; mm; mm &= mm - 1) {
         const int k = __ffs(mm) - 1;
         const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
@@ -423,16 +740,15 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
           m4 = fmaf(r1, dy, m4);
           m5 = fmaf(r0 * dy, dy, m5);
         }
-        // second moments about S^, then into the lane's compensated totals
+        // second moments about S^, then into the lane's totals
         m3 = fmaf(-sxx, m0, m3);
         m4 = fmaf(-sxy, m0, m4);
         m5 = fmaf(-syy, m0, m5);
-        kahan2(s01, c01, make_float2(m0, m1));
-        kahan2(s23, c23, make_float2(m2, m3));
-        kahan2(s45, c45, make_float2(m4, m5));
+        s01 = add2(s01, make_float2(m0, m1));
+        s23 = add2(s23, make_float2(m2, m3));
+        s45 = add2(s45, make_float2(m4, m5));
       }
-      float m0 = s01.x - c01.x, m1 = s01.y - c01.y, m2 = s23.x - c23.x;
-      float m3 = s23.y - c23.y, m4 = s45.x - c45.x, m5 = s45.y - c45.y;
+      float m0 = s01.x, m1 = s01.y, m2 = s23.x, m3 = s23.y, m4 = s45.x, m5 = s45.y;
 #pragma unroll
       for (int o = 1; o < kLpr; o <<= 1) {
         m0 += __shfl_xor_sync(gmask, m0, o);
@@ -444,12 +760,12 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       }
       if (gq == 0) {
         double *mo = mb + (int64_t)sj[warp][slot] * 6;
-        atomicAdd(mo + 0, f32_to_f64(m0));
-        atomicAdd(mo + 1, f32_to_f64(m1));
-        atomicAdd(mo + 2, f32_to_f64(m2));
-        atomicAdd(mo + 3, f32_to_f64(m3));
-        atomicAdd(mo + 4, f32_to_f64(m4));
-        atomicAdd(mo + 5, f32_to_f64(m5));
+        atomicAdd(mo + 0, (double)m0);
+        atomicAdd(mo + 1, (double)m1);
+        atomicAdd(mo + 2, (double)m2);
+        atomicAdd(mo + 3, (double)m3);
+        atomicAdd(mo + 4, (double)m4);
+        atomicAdd(mo + 5, (double)m5);
       }
     }
     int wn = 0;
@@ -458,13 +774,32 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   }
 }
 
-cudaError_t launch_raster_bwd(const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+// The backward's kernel configurations (the autotuner's search space):
+// lanes per record and records per lane per warp window.
+static const BwdCfg kBwdCfgs[] = {
+    {2, 4, "2 lanes per record, 128-record warp windows"},
+    {4, 4, "4 lanes per record, 128-record warp windows"},
+    {1, 4, "1 lane per record, 128-record warp windows"},
+};
+int bwd_config_count() { return (int)(sizeof(kBwdCfgs) / sizeof(kBwdCfgs[0])); }
+const BwdCfg &bwd_config(int i) { return kBwdCfgs[i]; }
+
+cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, cudaStream_t st) {
+  if (cfg < 0 || cfg >= bwd_config_count()) return cudaErrorInvalidValue;
   int nt = d / kTile;
   dim3 grid(nt * nt, B);
-  raster_bwd_kernel<kBwdLanes, kBwdPer><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start,
-                                                                  cap, M, d, l2tau, dproj, mom);
+  const int lanes = kBwdCfgs[cfg].lanes;
+  if (lanes == 2)
+    raster_bwd_kernel<2, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                       l2tau, dproj, mom);
+  else if (lanes == 4)
+    raster_bwd_kernel<4, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                       l2tau, dproj, mom);
+  else
+    raster_bwd_kernel<1, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                       l2tau, dproj, mom);
   return cudaGetLastError();
 }
 
@@ -538,7 +873,7 @@ __global__ void __launch_bounds__(128) dense_bwd_kernel(const Rec *__restrict__ 
   }
   double *mm = mom + ((int64_t)b * M + j) * 6;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) mm[k] = f32_to_f64(m[k]);
+  for (int k = 0; k < 6; ++k) mm[k] = (double)m[k];
 }
 
 cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2tau, float *proj,
