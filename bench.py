@@ -445,6 +445,7 @@ def time_secondary(w, dev, stream, flush, steps: int, warm: int):
         ctx.gem_forward(D["params"], D["R"], D["t"], D["images"], loss, ctf_params=D["ctf_params"])
         ctx.gem_backward(grad)
 
+    tuned = ctx.gem_autotune(D["params"], D["R"], D["t"], reps=3)
     for _ in range(warm):
         flush.zero_()
         step()
@@ -469,8 +470,10 @@ def time_secondary(w, dev, stream, flush, steps: int, warm: int):
         for k in stage:
             stage[k] += m[k] / n
     ctx.close()
+    fn, bn = binding.raster_configs()
     return {"value": w.B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "config": workload_config(w), "stages_ms": stage, "timing": "device (CUDA events), L2 flushed"}
+            "config": workload_config(w), "stages_ms": stage, "timing": "device (CUDA events), L2 flushed",
+            "raster_configs": {"forward": fn[tuned[0]], "backward": bn[tuned[1]]}}
 
 
 # --------------------------------------------------------------- main ------
@@ -511,6 +514,13 @@ def main():
         X = D if X is None else X
         ctx.gem_forward(X["params"], X["R"], X["t"], X["images"], loss, ctf_params=X["ctf_params"])
         ctx.gem_backward(grad)
+
+    # the rasterisers' kernel configurations for this shape (the library's
+    # autotuner, once, outside every timed region)
+    tuned = ctx.gem_autotune(D["params"], D["R"], D["t"], reps=3)
+    fwd_names, bwd_names = binding.raster_configs()
+    raster_cfg = {"forward": fwd_names[tuned[0]], "backward": bwd_names[tuned[1]],
+                  "chosen_by": "gem_autotune (every configuration timed 3x on this shape)"}
 
     warm = max(args.warmup, 3)
     for _ in range(warm):
@@ -816,7 +826,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(w), "clocks": clk, "e2e": e2e,
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "plain": plain,
-            "stages_ms": per_stage, "loss": step_loss, "parity": parity, "secondary": secondary,
+            "stages_ms": per_stage, "raster_configs": raster_cfg, "loss": step_loss, "parity": parity,
+            "secondary": secondary,
             "query": query, "train": train,
         }
         print(json.dumps(line), flush=True)

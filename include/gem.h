@@ -109,9 +109,11 @@ const char *gem_last_error(const gem_ctx *ctx);
 /* Change the stream later calls use. */
 int gem_set_stream(gem_ctx *ctx, void *cuda_stream);
 
-/* Synchronise the context's stream and return GEM_OK, GEM_ECAPACITY (the
- * last projection needed more than max_pairs list entries; its outputs are
- * incomplete) or GEM_ECUDA.  Clears the status word. */
+/* Synchronise the context's stream and return GEM_OK, GEM_ECAPACITY (a
+ * projection since the last read needed more than max_pairs list entries:
+ * its lists are incomplete, so the rasterisers treat every list of that
+ * call as empty, and its projection, and a backward of it, come out zero)
+ * or GEM_ECUDA.  Clears the status word. */
 int gem_status(gem_ctx *ctx);
 
 /* ---- steps of the hot path -------------------------------------------- */

@@ -101,7 +101,7 @@ struct gem_ctx {
 
 // The configurations used when neither the context nor the autotuner's cache
 // names one (the fastest measured on the benchmark workloads).
-constexpr int kDefaultFwdCfg = 0;
+constexpr int kDefaultFwdCfg = 4;  // block-aligned, 256-record windows, persistent longest-first
 constexpr int kDefaultBwdCfg = 0;
 
 // The autotuner's choices, shared by every context of the process: keyed by
@@ -411,8 +411,9 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
     c->bins_l2tau = c->l2tau;
   }
   {
-    StageScope sc(c, GEM_STAGE_RASTER_FWD, 1);
-    if ((e = launch_raster_fwd(active_fwd(c, B, M), c->rec, c->bin.list, c->bin.lmask,
+    const int fc = active_fwd(c, B, M);
+    StageScope sc(c, GEM_STAGE_RASTER_FWD, fwd_config(fc).persistent ? 2 : 1);
+    if ((e = launch_raster_fwd(fc, c->rec, c->bin.list, c->bin.lmask,
                                c->bin.tile_start, c->bin.cap, M, B, g.d, c->l2tau, proj, c->order,
                                c->next_tile, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "raster_fwd");

@@ -546,7 +546,10 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
 __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     const uint32_t *__restrict__ perm, int64_t M, int d, int nch,
     const uint32_t *__restrict__ tcnt, const int64_t *__restrict__ tile_start, BinScratch bs) {
-  extern __shared__ __align__(16) uint32_t bm[];  // [T][8] bitmaps, then int64 list base [T]
+  // bitmaps word-major, [8][T]: a warp's hits are mostly one Gaussian's
+  // neighbouring tiles, which then fall in neighbouring banks; then the
+  // int64 list base of each tile [T]
+  extern __shared__ __align__(16) uint32_t bm[];
   __shared__ uint32_t sj[kChunkT];   // Gaussian index of each slot
   const int c = blockIdx.x, b = blockIdx.y;
   const int nt = d / kTile, T = nt * nt;
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     const uint64_t h = hr[i];
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
-    atomicOr(&bm[t * 8 + (o >> 5)], 1u << (o & 31));
+    atomicOr(&bm[(o >> 5) * T + t], 1u << (o & 31));
   }
   __syncthreads();
   // list base of every tile the chunk hits: the tile's start plus the
@@ -572,17 +575,17 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     uint32_t any = 0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) any |= bm[i * 8 + q];
+    for (int q = 0; q < 8; ++q) any |= bm[q * T + i];
     if (any) tb[i] = tile_start[(int64_t)b * T + i] + coff[(int64_t)i * nch];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     const uint64_t h = hr[i];
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
-    const uint32_t *bw = bm + t * 8;
+    const uint32_t *bw = bm + t;
     const int word = o >> 5;
-    uint32_t rank = __popc(bw[word] & ((1u << (o & 31)) - 1u));
-    for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk]);
+    uint32_t rank = __popc(bw[word * T] & ((1u << (o & 31)) - 1u));
+    for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk * T]);
     const int64_t pos = tb[t] + rank;
     if (pos < bs.cap) {
       bs.list[pos] = sj[o];
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   }
 }
 
-// Bitmaps (8 words) and list base (8 bytes) per tile.
+// Bitmaps (8 words, word-major) and list base (8 bytes) per tile.
 static int tile_smem_bytes(int d) {
   int nt = d / kTile;
   return nt * nt * (8 * (int)sizeof(uint32_t) + (int)sizeof(int64_t));

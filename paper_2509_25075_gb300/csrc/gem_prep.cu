@@ -351,7 +351,13 @@ cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M,
                             const float *R, const float *t, float apix, int d, int norm_mode,
                             int shape, double *mom, float *part, int nbg, float *grad,
                             cudaStream_t st) {
-  int per = (B + nbg - 1) / nbg;
+  // views per thread: enough (Gaussian, view-group) threads to fill the GPU
+  // (about 2^20), and no more, so that the per-Gaussian reads, the
+  // view-independent chain rule and the partial sums are shared by as many
+  // views as possible
+  const int64_t want = ((int64_t)1 << 20) / (M > 0 ? M : 1) + 1;
+  const int use = (int)(want < nbg ? want : nbg);
+  int per = (B + use - 1) / use;
   int groups = (B + per - 1) / per;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)groups);
   prep_bwd_kernel<<<grid, 128, 0, st>>>(params, gp, M, B, R, t, apix, d, norm_mode, shape, mom,

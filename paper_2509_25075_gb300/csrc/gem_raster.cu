@@ -82,6 +82,9 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
   s = min(s, e);
+  // lists that overflowed their capacity are incomplete: every list counts
+  // as empty (the status word reports it)
+  if (tile_start[(int64_t)gridDim.y * T] > cap) e = s;
   const Rec *rb = rec + (int64_t)b * M;
   const unsigned lt = (1u << lane) - 1u;
   // pixels owned across windows: two columns of one row of block ob
@@ -97,8 +100,11 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
     for (int u = 0; u < kSub; ++u) {
       const int slot = u * kThreads + tid;
       m[u] = 0;
-      if (slot < n) {
-        const Rec *rp = rb + list[base + slot];
+      // an entry whose Gaussian index is out of range (a list position left
+      // unwritten when the lists overflowed their capacity) counts as empty
+      const uint32_t jj = slot < n ? list[base + slot] : 0u;
+      if (slot < n && jj < (uint64_t)M) {
+        const Rec *rp = rb + jj;
         const float4 ra = rp->a;
         const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
         m[u] = lmask[base + slot];
@@ -321,6 +327,9 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
     int64_t e = tile_start[bt + 1];
     e = min(e, cap);
     s = min(s, e);
+    // lists that overflowed their capacity are incomplete: every list
+    // counts as empty (the status word reports it)
+    if (tile_start[order == nullptr ? (int64_t)gridDim.y * T : (int64_t)ntiles] > cap) e = s;
     const Rec *rb = rec + (int64_t)b * M;
     float2 own0 = make_float2(0.f, 0.f), own1 = make_float2(0.f, 0.f);  // Kahan (sum, comp)
     for (int64_t base = s; base < e; base += kWinW) {
@@ -331,8 +340,12 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
       for (int u = 0; u < kSubW; ++u) {
         const int slot = u * kThreads + tid;
         m[u] = 0;
-        if (slot < n) {
-          const Rec *rp = rb + list[base + slot];
+        // an entry whose Gaussian index is out of range (a list position
+        // left unwritten when the lists overflowed their capacity) counts as
+        // empty
+        const uint32_t jj = slot < n ? list[base + slot] : 0u;
+        if (slot < n && jj < (uint64_t)M) {
+          const Rec *rp = rb + jj;
           const float4 ra = rp->a;
           const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
           m[u] = lmask[base + slot];
@@ -632,6 +645,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
   s = min(s, e);
+  if (tile_start[(int64_t)gridDim.y * T] > cap) e = s;  // overflowed: every list empty
   const Rec *rb = rec + (int64_t)b * M;
   double *mb = mom + (int64_t)b * M * 6;
   int *h = hist[warp];
@@ -654,7 +668,9 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       m[q] = 0;
       if (i < e) {
         j[q] = list[i];
-        m[q] = lmask[i];
+        // an out-of-range index (an entry left unwritten when the lists
+        // overflowed their capacity) counts as empty
+        m[q] = j[q] < (uint64_t)M ? lmask[i] : 0u;
       }
       atomicAdd(&h[__popc(m[q])], 1);
     }

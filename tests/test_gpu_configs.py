@@ -44,7 +44,8 @@ def test_every_forward_config_matches_oracle(w, fwd):
     ctx = _ctx(w)
     ctx.gem_set_raster_config(fwd, -1)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
-    ctx.gem_project(gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"]), proj)
+    args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    ctx.gem_project(*args, proj)
     assert ctx.gem_status() == 0
     ref = oracle.project(inp["params"], inp["R"], inp["t"], w.d, w.apix, w.tau)
     gt.assert_proj_close(proj.cpu().numpy(), ref, w.tau, gt.borderline_pairs(inp, w, w.tau))
@@ -66,7 +67,8 @@ def test_persistent_forward_is_bitwise_the_per_tile_forward():
         ctx = _ctx(w)
         ctx.gem_set_raster_config(i, -1)
         proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
-        ctx.gem_project(gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"]), proj)
+        args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+        ctx.gem_project(*args, proj)
         assert ctx.gem_status() == 0
         out[name] = proj.cpu().numpy()
         ctx.close()
@@ -83,7 +85,9 @@ def test_every_backward_config_matches_oracle(w, bwd):
     ctx = _ctx(w)
     ctx.gem_set_raster_config(-1, bwd)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
-    ctx.gem_project(gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"]), proj)
+    # params, R and t stay referenced: the backward reads them again
+    args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    ctx.gem_project(*args, proj)
     g = syn.smooth_field(w) * 1e-3
     grad = torch.empty(w.M, 11, device=gt.DEV)
     ctx.gem_project_backward(gt.to_dev(g), grad)

@@ -25,7 +25,8 @@ def test_fullsize_projection_sampled_pixels(name):
     inp = gt.inputs(w)
     ctx = _ctx(w)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
-    ctx.gem_project(gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"]), proj)
+    args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    ctx.gem_project(*args, proj)
     assert ctx.gem_status() == 0
     rng = np.random.default_rng(100)
     # half the samples near the particle (the image centre), half anywhere
@@ -84,7 +85,9 @@ def test_fullsize_gradient_sampled_gaussians(name):
     g = syn.smooth_field(w) * 1e-3
     ctx = _ctx(w)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
-    ctx.gem_project(gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"]), proj)
+    # params, R and t stay referenced: the backward reads them again
+    args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    ctx.gem_project(*args, proj)
     grad = torch.empty(w.M, 11, device=gt.DEV)
     ctx.gem_project_backward(gt.to_dev(g), grad)
     assert ctx.gem_status() == 0
