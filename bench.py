@@ -113,6 +113,9 @@ def parse():
     ap.add_argument("--secondary", default="A2",
                     help="comma-separated workloads also timed on the device (N=1 only; '' for none)")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled check against the oracle")
+    ap.add_argument("--raster-config", default=None,
+                    help="'F,B': use forward / backward rasteriser configurations F, B (indices of "
+                         "binding.raster_configs()) instead of the autotuner's choice")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain dense form")
     ap.add_argument("--no-query", action="store_true",
                     help="skip timing the density query, FSC, training iteration and nearest neighbours")
@@ -517,10 +520,15 @@ def main():
 
     # the rasterisers' kernel configurations for this shape (the library's
     # autotuner, once, outside every timed region)
-    tuned = ctx.gem_autotune(D["params"], D["R"], D["t"], reps=3)
     fwd_names, bwd_names = binding.raster_configs()
-    raster_cfg = {"forward": fwd_names[tuned[0]], "backward": bwd_names[tuned[1]],
-                  "chosen_by": "gem_autotune (every configuration timed 3x on this shape)"}
+    if args.raster_config:
+        tuned = tuple(int(x) for x in args.raster_config.split(","))
+        ctx.gem_set_raster_config(*tuned)
+        chosen = "--raster-config"
+    else:
+        tuned = ctx.gem_autotune(D["params"], D["R"], D["t"], reps=3)
+        chosen = "gem_autotune (every configuration timed 3x on this shape)"
+    raster_cfg = {"forward": fwd_names[tuned[0]], "backward": bwd_names[tuned[1]], "chosen_by": chosen}
 
     warm = max(args.warmup, 3)
     for _ in range(warm):

@@ -73,7 +73,7 @@ struct gem_ctx {
   // else the default
   int fwd_cfg = -1, bwd_cfg = -1;
   uint32_t *order = nullptr;     // [max_B * T] tile order of the persistent forward
-  unsigned *next_tile = nullptr;  // [1] its work counter
+  unsigned *next_tile = nullptr;  // [2] work counters of the persistent forward, backward
   float *tune_grad = nullptr;     // [max_M][11] gradient the autotuner's backward writes
   std::vector<void *> allocs;
   // per-stage timing (events recorded around each stage when enabled)
@@ -276,7 +276,7 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->Z, (size_t)g.max_B * d * d) && alloc(c, &c->tw, (size_t)d) &&
             alloc(c, &c->lossp, (size_t)g.max_B * (ctf_partials(d) + 1)) && alloc(c, &c->status, 1) &&
             alloc(c, &c->kept, 2) &&
-            alloc(c, &c->order, (size_t)g.max_B * c->T) && alloc(c, &c->next_tile, 1);
+            alloc(c, &c->order, (size_t)g.max_B * c->T) && alloc(c, &c->next_tile, 2);
   // nearest-neighbour grid: at most 2 max_M + 64 cells
   c->knn.cap = 2 * g.max_M + 64;
   ok = ok && alloc(c, &c->knn.part, 608 * 6) && alloc(c, &c->knn.grid, 1) &&
@@ -469,7 +469,8 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
   // the whole buffer, should an earlier pass have stopped before clearing it
   size_t mbytes = (size_t)g.max_B * g.max_M * 6 * sizeof(double);
   {
-    StageScope sc(c, GEM_STAGE_RASTER_BWD, 1);
+    StageScope sc(c, GEM_STAGE_RASTER_BWD,
+                  1 + (!dense && bwd_config(active_bwd(c, c->B, c->M)).persistent ? 1 : 0));
     if (!dense && !c->mom_clean && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "moment clear");
     c->mom_clean = false;
@@ -478,7 +479,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     else
       e = launch_raster_bwd(active_bwd(c, c->B, c->M), c->rec, c->bin.list, c->bin.lmask,
                             c->bin.tile_start, c->bin.cap, c->M, c->B, g.d, c->l2tau, dproj, c->mom,
-                            c->stream);
+                            c->order, c->next_tile + 1, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
   StageScope sc(c, GEM_STAGE_PREP_BWD, 2);

@@ -277,16 +277,18 @@ cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, con
                               float l2tau, float *proj, uint32_t *order, unsigned *next_tile,
                               cudaStream_t st);
 // A configuration of the backward rasteriser: lanes sharing one record,
-// records per lane per warp window.
+// records per lane per warp window, persistent grid (tiles longest-first
+// from a counter; order [B*T] and next_tile [1] are its scratch).
 struct BwdCfg {
-  int lanes, per;
+  int lanes, per, persistent;
   const char *name;
 };
 int bwd_config_count();
 const BwdCfg &bwd_config(int i);
 cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, const float *dproj, double *mom, cudaStream_t st);
+                              float l2tau, const float *dproj, double *mom, uint32_t *order,
+                              unsigned *next_tile, cudaStream_t st);
 cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
                               const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
                               int64_t M, int B, int d, float l2tau, unsigned long long *kept,

@@ -499,20 +499,33 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
   }
 }
 
-// Longest-first order of the B*T tiles for the persistent form: a counting
+// Longest-first order of the B*T tiles for the persistent forms: a counting
 // sort of the tiles by the bit length of their list length (one CTA; 32
 // classes, longest class first, ties in any order) and the work counter
-// reset.  Which tile runs when changes nothing in its result.
+// reset.  Which tile runs when changes nothing in its result.  Lanes of a
+// warp with the same class share one shared-memory atomic (tiles of one
+// batch mostly fall in two or three classes).
+__device__ __forceinline__ int tile_class(const int64_t *__restrict__ tile_start, int i) {
+  const int64_t len = tile_start[i + 1] - tile_start[i];
+  return 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
+}
+
 __global__ void __launch_bounds__(1024) tile_order_kernel(const int64_t *__restrict__ tile_start,
                                                          int ntiles, uint32_t *__restrict__ order,
                                                          unsigned *__restrict__ next_tile) {
   __shared__ unsigned hist[32], cur[32];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
-    const int64_t len = tile_start[i + 1] - tile_start[i];
-    const int c = 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
-    atomicAdd(&hist[c], 1u);
+  // every warp runs the same number of rounds, so all its lanes take part in
+  // each match
+  const int rounds = (ntiles + blockDim.x - 1) / blockDim.x;
+  for (int r = 0; r < rounds; ++r) {
+    const int i = r * blockDim.x + threadIdx.x;
+    const int c = i < ntiles ? tile_class(tile_start, i) : 32 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (c < 32 && (peers & lt) == 0) atomicAdd(&hist[c], (unsigned)__popc(peers));
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -524,10 +537,15 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int64_t *__restr
     *next_tile = 0u;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) {
-    const int64_t len = tile_start[i + 1] - tile_start[i];
-    const int c = 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
-    order[atomicAdd(&cur[c], 1u)] = (uint32_t)i;
+  for (int r = 0; r < rounds; ++r) {
+    const int i = r * blockDim.x + threadIdx.x;
+    const int c = i < ntiles ? tile_class(tile_start, i) : 32 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (c < 32 && lane == leader) base = atomicAdd(&cur[c], (unsigned)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c < 32) order[base + __popc(peers & lt)] = (uint32_t)i;
   }
 }
 
@@ -616,7 +634,8 @@ template <int kLpr, int kPer>
 __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
     const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
-    int64_t M, int d, float l2tau, const float *__restrict__ dproj, double *__restrict__ mom) {
+    int64_t M, int d, float l2tau, const float *__restrict__ dproj, double *__restrict__ mom,
+    const uint32_t *__restrict__ order, int ntiles, unsigned *__restrict__ next_tile) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kWW = 32 * kPer;     // records per warp window
   constexpr int kRpr = 32 / kLpr;    // records per round
@@ -628,11 +647,28 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   __shared__ unsigned short smask[kWarps][kWW];
   __shared__ int hist[kWarps][32];
   __shared__ int next_win;
+  __shared__ int tile_sh;
   const int nt = d / kTile, T = nt * nt;
-  const int t = blockIdx.x, b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t total = tile_start[order == nullptr ? (int64_t)gridDim.y * T : (int64_t)ntiles];
+  // tiles come from the grid (order == nullptr) or, in the persistent form,
+  // from a shared counter over a longest-first order
+  for (int it = 0;; ++it) {
+  int bt;
+  if (order == nullptr) {
+    if (it > 0) break;
+    bt = blockIdx.y * T + blockIdx.x;
+  } else {
+    __syncthreads();  // every warp is done with the previous tile
+    if (threadIdx.x == 0) tile_sh = (int)atomicAdd(next_tile, 1u);
+    __syncthreads();
+    const int qq = tile_sh;
+    if (qq >= ntiles) break;
+    bt = (int)order[qq];
+  }
+  const int b = bt / T, t = bt - b * T;
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // g tile, stored block by block
   if (threadIdx.x < kTile * kTile / 4) {
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // pixel row, 4-column group
@@ -641,11 +677,11 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   }
   if (threadIdx.x == 0) next_win = kWarps;
   __syncthreads();
-  int64_t s = tile_start[(int64_t)b * T + t];
-  int64_t e = tile_start[(int64_t)b * T + t + 1];
+  int64_t s = tile_start[bt];
+  int64_t e = tile_start[bt + 1];
   e = min(e, cap);
   s = min(s, e);
-  if (tile_start[(int64_t)gridDim.y * T] > cap) e = s;  // overflowed: every list empty
+  if (total > cap) e = s;  // overflowed: every list empty
   const Rec *rb = rec + (int64_t)b * M;
   double *mb = mom + (int64_t)b * M * 6;
   int *h = hist[warp];
@@ -788,34 +824,61 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     if (lane == 0) wn = atomicAdd(&next_win, 1);
     base = s + (int64_t)kWW * __shfl_sync(0xffffffffu, wn, 0);
   }
+  }  // tiles
 }
 
 // The backward's kernel configurations (the autotuner's search space):
-// lanes per record and records per lane per warp window.
+// lanes per record, records per lane per warp window, persistent grid.
 static const BwdCfg kBwdCfgs[] = {
-    {2, 4, "2 lanes per record, 128-record warp windows"},
-    {4, 4, "4 lanes per record, 128-record warp windows"},
-    {1, 4, "1 lane per record, 128-record warp windows"},
+    {2, 4, 0, "2 lanes per record, 128-record warp windows"},
+    {4, 4, 0, "4 lanes per record, 128-record warp windows"},
+    {1, 4, 0, "1 lane per record, 128-record warp windows"},
+    {2, 4, 1, "2 lanes per record, 128-record warp windows, persistent longest-first"},
+    {1, 4, 1, "1 lane per record, 128-record warp windows, persistent longest-first"},
 };
 int bwd_config_count() { return (int)(sizeof(kBwdCfgs) / sizeof(kBwdCfgs[0])); }
 const BwdCfg &bwd_config(int i) { return kBwdCfgs[i]; }
 
+template <int kLpr>
+static void launch_bwd_lanes(dim3 grid, const Rec *rec, const uint32_t *list,
+                             const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+                             int64_t M, int d, float l2tau, const float *dproj, double *mom,
+                             const uint32_t *order, int ntiles, unsigned *next_tile,
+                             cudaStream_t st) {
+  raster_bwd_kernel<kLpr, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+                                                        l2tau, dproj, mom, order, ntiles,
+                                                        next_tile);
+}
+
 cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
-                              float l2tau, const float *dproj, double *mom, cudaStream_t st) {
+                              float l2tau, const float *dproj, double *mom, uint32_t *order,
+                              unsigned *next_tile, cudaStream_t st) {
   if (cfg < 0 || cfg >= bwd_config_count()) return cudaErrorInvalidValue;
-  int nt = d / kTile;
+  const BwdCfg &c = kBwdCfgs[cfg];
+  if (c.persistent && (order == nullptr || next_tile == nullptr)) return cudaErrorInvalidValue;
+  const int nt = d / kTile, ntiles = nt * nt * B;
   dim3 grid(nt * nt, B);
-  const int lanes = kBwdCfgs[cfg].lanes;
-  if (lanes == 2)
-    raster_bwd_kernel<2, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                       l2tau, dproj, mom);
-  else if (lanes == 4)
-    raster_bwd_kernel<4, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                       l2tau, dproj, mom);
+  const uint32_t *ord = nullptr;
+  unsigned *ctr = nullptr;
+  if (c.persistent) {
+    tile_order_kernel<<<1, 1024, 0, st>>>(tile_start, ntiles, order, next_tile);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = dim3((unsigned)max(1, min(ntiles, sms * 8)), 1);
+    ord = order;
+    ctr = next_tile;
+  }
+  if (c.lanes == 2)
+    launch_bwd_lanes<2>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                        ntiles, ctr, st);
+  else if (c.lanes == 4)
+    launch_bwd_lanes<4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                        ntiles, ctr, st);
   else
-    raster_bwd_kernel<1, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                       l2tau, dproj, mom);
+    launch_bwd_lanes<1>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                        ntiles, ctr, st);
   return cudaGetLastError();
 }
 

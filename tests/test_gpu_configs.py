@@ -130,3 +130,29 @@ def test_autotune_records_a_choice_that_computes_the_same_step():
         ctx.gem_set_raster_config(nf, 0)
     ctx.close()
     other.close()
+
+
+def test_persistent_backward_matches_the_per_tile_backward():
+    """The persistent backward runs the same tile code in another order; the
+    float64 moments are sums of the same partials in another order, so the
+    gradients agree to float rounding of float64 sums (here: 1e-6)."""
+    w = CASES[2]
+    inp = gt.inputs(w)
+    names = _n_configs()[1]
+    g = gt.to_dev(syn.smooth_field(w) * 1e-3)
+    out = {}
+    for i, name in enumerate(names):
+        ctx = _ctx(w)
+        ctx.gem_set_raster_config(-1, i)
+        proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
+        args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+        ctx.gem_project(*args, proj)
+        grad = torch.empty(w.M, 11, device=gt.DEV)
+        ctx.gem_project_backward(g, grad)
+        assert ctx.gem_status() == 0
+        out[name] = grad.cpu().numpy().astype(np.float64)
+        ctx.close()
+    for name, gr in out.items():
+        if "persistent" in name:
+            base = out[name.split(", persistent")[0]]
+            assert np.linalg.norm(gr - base) <= 1e-6 * np.linalg.norm(base)
