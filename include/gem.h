@@ -379,9 +379,10 @@ int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float *proj, con
 /* Both rasterisers come in several kernel configurations that compute the
  * same result (bitwise, for a given configuration; within float rounding
  * across configurations): the forward (step a3) as equal runs of items
- * across blocks or runs aligned to blocks, with 256- or 512-record windows,
- * a per-tile grid or a persistent grid that takes tiles longest-first from
- * a counter; the backward (a5) with 1, 2 or 4 lanes per record.  Which is
+ * across blocks or runs aligned to blocks, at 8 or 9 CTAs per SM, on a
+ * per-tile grid or a persistent grid that takes tiles longest-first from a
+ * counter; the backward (a5) with 1 or 2 lanes per record, on either grid.
+ * Which is
  * fastest depends on the image side, the batch and the Gaussians' sizes.
  * Counts of each kind (kind 0: forward, 1: backward); a configuration's
  * description ("" if out of range). */

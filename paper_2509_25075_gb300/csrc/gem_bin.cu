@@ -369,8 +369,7 @@ __device__ __forceinline__ unsigned candidate_mask(const ChunkStage &S, bool sta
 }
 
 // Per chunk of 256 Gaussians (depth order) of image b: how many hit each
-// tile, written transposed, tcnt[b][t][c], so that each tile's column is
-// contiguous for the scan; and every hit, (slot o in the chunk, tile, 4x4-block
+// tile, tcnt[b][c][t] (one contiguous row per chunk); and every hit, (slot o in the chunk, tile, 4x4-block
 // mask), in a run of hits[] claimed from a shared cursor, so that the scatter
 // pass repeats none of the geometry.  A candidate tile is a hit when its
 // block mask is not empty.  The run's contents and layout (threads in
@@ -452,33 +451,42 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     --nh;
   }
   __syncthreads();
-  uint32_t *out = tcnt + (int64_t)b * T * nch + c;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) out[(int64_t)i * nch] = tc[i];
+  uint32_t *out = tcnt + ((int64_t)b * nch + c) * T;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) out[i] = tc[i];
 }
 
-// One warp per (image, tile): exclusive scan of the chunk counts in place;
-// the tile total goes to tile_n[b * T + t].
-__global__ void __launch_bounds__(256) tile_scan_cols_kernel(uint32_t *__restrict__ tcnt,
-                                                             int nch, int64_t ncols,
-                                                             int64_t *__restrict__ tile_n) {
-  int64_t col = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (col >= ncols) return;
-  uint32_t *p = tcnt + col * nch;
-  uint32_t carry = 0;
-  for (int c0 = 0; c0 < nch; c0 += 32) {
-    int c = c0 + lane;
-    uint32_t v = c < nch ? p[c] : 0;
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
+// Exclusive scan over the chunks of every (image, tile) column of
+// tcnt[b][c][t], in place; the column totals go to tile_n[b * T + t].  A
+// CTA takes 32 tiles of one image (one per lane, so every access reads 32
+// consecutive counts of a chunk row) and its 8 warps take 8 consecutive
+// ranges of chunks: a pass of range sums, their exclusive prefix across the
+// warps, then a pass that writes the prefix.
+constexpr int kScanWarps = 8;
+__global__ void __launch_bounds__(32 * kScanWarps) tile_scan_cols_kernel(
+    uint32_t *__restrict__ tcnt, int nch, int T, int64_t *__restrict__ tile_n) {
+  __shared__ uint32_t part[kScanWarps][32];
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  const bool act = t < T;
+  uint32_t *col = tcnt + (int64_t)b * nch * T + t;
+  const int per = (nch + kScanWarps - 1) / kScanWarps;
+  const int c0 = min(nch, warp * per), c1 = min(nch, c0 + per);
+  uint32_t sum = 0;
+  if (act)
+    for (int c = c0; c < c1; ++c) sum += col[(int64_t)c * T];
+  part[warp][lane] = sum;
+  __syncthreads();
+  uint32_t run = 0;
+  for (int w = 0; w < warp; ++w) run += part[w][lane];
+  if (act) {
+    for (int c = c0; c < c1; ++c) {
+      const uint32_t v = col[(int64_t)c * T];
+      col[(int64_t)c * T] = run;
+      run += v;
     }
-    if (c < nch) p[c] = carry + inc - v;
-    carry += __shfl_sync(0xffffffffu, inc, 31);
+    if (warp == kScanWarps - 1) tile_n[(int64_t)b * T + t] = run;
   }
-  if (lane == 0) tile_n[col] = carry;
 }
 
 // In-place exclusive scan of n counts (one block of 1024), total in x[n].
@@ -571,12 +579,12 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   __syncthreads();
   // list base of every tile the chunk hits: the tile's start plus the
   // chunk's offset in it
-  const uint32_t *coff = tcnt + (int64_t)b * T * nch + c;
+  const uint32_t *coff = tcnt + ((int64_t)b * nch + c) * T;
   for (int i = threadIdx.x; i < T; i += blockDim.x) {
     uint32_t any = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) any |= bm[q * T + i];
-    if (any) tb[i] = tile_start[(int64_t)b * T + i] + coff[(int64_t)i * nch];
+    if (any) tb[i] = tile_start[(int64_t)b * T + i] + coff[i];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
@@ -637,8 +645,8 @@ cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, in
   if ((e = cudaMemsetAsync(s.hit_ctr, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
   tile_count_kernel<<<g, 256, cnt_smem, st>>>(rec, perm, M, d, l2tau, nch, s.tcnt, s);
   int64_t ncols = (int64_t)B * T;
-  tile_scan_cols_kernel<<<(unsigned)((ncols + 7) / 8), 256, 0, st>>>(s.tcnt, nch, ncols,
-                                                                      s.tile_start);
+  tile_scan_cols_kernel<<<dim3((unsigned)((T + 31) / 32), (unsigned)B), 32 * kScanWarps, 0, st>>>(
+      s.tcnt, nch, T, s.tile_start);
   scan_tiles_kernel<<<1, 1024, 0, st>>>(s.tile_start, ncols, s.cap, s.status);
   tile_scatter_kernel<<<g, 256, tile_smem_bytes(d), st>>>(perm, M, d, nch, s.tcnt, s.tile_start, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -240,7 +240,7 @@ struct BinScratch {
   uint32_t *packed;        // [B][M] (high key byte << 24 | index) after the first pass
   uint32_t *perm;          // [B][M] Gaussian indices in depth order
   uint32_t *dcnt;          // [B][nchD][256]
-  uint32_t *tcnt;          // [B][T][nchT]
+  uint32_t *tcnt;          // [B][nchT][T] per chunk: hits per tile, then offsets
   int64_t *tile_start;     // [B*T + 1]
   uint32_t *list;          // [cap] Gaussian index per entry
   uint16_t *lmask;         // [cap] 4x4-block mask per entry

@@ -500,12 +500,17 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
 }
 
 // Longest-first order of the B*T tiles for the persistent forms: a counting
-// sort of the tiles by the bit length of their list length (one CTA; 32
-// classes, longest class first, ties in any order) and the work counter
-// reset.  Which tile runs when changes nothing in its result.  Lanes of a
-// warp with the same class share one shared-memory atomic (tiles of one
-// batch mostly fall in two or three classes).
-__device__ __forceinline__ int tile_class(const int64_t *__restrict__ tile_start, int i) {
+// sort of the tiles by the bit length of their list length (32 classes,
+// longest class first), so that the longest tiles start in the first wave
+// and the launch does not end waiting for one.  One CTA walks the tiles in
+// index order, 1024 at a time, so within a class the order follows the
+// index (image after image) up to the order of the warps of one round.  CTA
+// 0 also resets the work counter.  Which tile runs when changes nothing in
+// its result.  Lanes of a warp with the same class share one shared-memory
+// atomic (tiles mostly fall in a few classes).  (Ordering image by image,
+// longest tile first within each image, kept more records in L2 but ran
+// slower: the long tiles of the last images started late.)
+__device__ __forceinline__ int tile_class(const int64_t *__restrict__ tile_start, int64_t i) {
   const int64_t len = tile_start[i + 1] - tile_start[i];
   return 31 - min(31, 64 - __clzll((unsigned long long)max(len, (int64_t)0)));
 }
@@ -546,6 +551,7 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int64_t *__restr
     if (c < 32 && lane == leader) base = atomicAdd(&cur[c], (unsigned)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
     if (c < 32) order[base + __popc(peers & lt)] = (uint32_t)i;
+    __syncthreads();  // rounds in index order
   }
 }
 
@@ -554,9 +560,8 @@ static const FwdCfg kFwdCfgs[] = {
     {0, 2, 9, 0, "runs, 256-record windows, 9 CTAs/SM"},
     {1, 2, 9, 0, "aligned, 256-record windows, 9 CTAs/SM"},
     {1, 2, 8, 0, "aligned, 256-record windows, 8 CTAs/SM"},
-    {1, 4, 5, 0, "aligned, 512-record windows, 5 CTAs/SM"},
     {1, 2, 9, 1, "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first"},
-    {1, 4, 5, 1, "aligned, 512-record windows, 5 CTAs/SM, persistent longest-first"},
+    {1, 2, 8, 1, "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first"},
 };
 int fwd_config_count() { return (int)(sizeof(kFwdCfgs) / sizeof(kFwdCfgs[0])); }
 const FwdCfg &fwd_config(int i) { return kFwdCfgs[i]; }
@@ -600,13 +605,10 @@ static cudaError_t launch_fwd_any(int cfg, const Rec *rec, const uint32_t *list,
                                                          l2tau, proj, kept);
     return cudaGetLastError();
   }
-  if (c.sub == 2 && c.minb == 9)
+  if (c.minb == 9)
     return launch_aligned<2, 9, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
                                         kept, order, next_tile, st);
-  if (c.sub == 2 && c.minb == 8)
-    return launch_aligned<2, 8, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
-                                        kept, order, next_tile, st);
-  return launch_aligned<4, 5, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+  return launch_aligned<2, 8, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
                                       kept, order, next_tile, st);
 }
 
@@ -640,7 +642,10 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   constexpr int kWW = 32 * kPer;     // records per warp window
   constexpr int kRpr = 32 / kLpr;    // records per round
   constexpr int kRows = 4 / kLpr;    // pixel rows of a block per lane
-  __shared__ float4 sg[16][4];  // g by 4x4 block: [block][row] = 4 pixels
+  // g by pixel row within a block and block: [row][block] = 4 pixels; the
+  // lanes of a warp read one row of many different blocks, which this
+  // layout spreads over the banks (two blocks eight apart share four banks)
+  __shared__ float4 sg[4][16];
   __shared__ float4 sa[kWarps][kWW];  // px, py, ca, cb
   __shared__ float2 sb[kWarps][kWW];  // cc, log2 A
   __shared__ uint32_t sj[kWarps][kWW];
@@ -672,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   // g tile, stored block by block
   if (threadIdx.x < kTile * kTile / 4) {
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // pixel row, 4-column group
-    sg[4 * (r >> 2) + q][r & 3] =
+    sg[r & 3][4 * (r >> 2) + q] =
         *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 + 4 * q);
   }
   if (threadIdx.x == 0) next_win = kWarps;
@@ -772,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
           // e = (ca dx + cb dy) dx + cc dy^2 + l2A, as in the forward's terms
           const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
           const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
-          const float4 g4 = sg[k][row0 + rr];
+          const float4 g4 = sg[row0 + rr][k];
           // w = g * value on kept pairs (value > tau), zero elsewhere
           const float2 gm01 = mul2(make_float2(g4.x, g4.y),
                                    make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
@@ -831,7 +836,6 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
 // lanes per record, records per lane per warp window, persistent grid.
 static const BwdCfg kBwdCfgs[] = {
     {2, 4, 0, "2 lanes per record, 128-record warp windows"},
-    {4, 4, 0, "4 lanes per record, 128-record warp windows"},
     {1, 4, 0, "1 lane per record, 128-record warp windows"},
     {2, 4, 1, "2 lanes per record, 128-record warp windows, persistent longest-first"},
     {1, 4, 1, "1 lane per record, 128-record warp windows, persistent longest-first"},
@@ -872,9 +876,6 @@ cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, con
   }
   if (c.lanes == 2)
     launch_bwd_lanes<2>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
-                        ntiles, ctr, st);
-  else if (c.lanes == 4)
-    launch_bwd_lanes<4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                         ntiles, ctr, st);
   else
     launch_bwd_lanes<1>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
