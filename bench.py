@@ -26,6 +26,7 @@ sampled Gaussians' gradients), each beside its tolerance.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -66,13 +67,20 @@ FP32_PER_CLK_PER_SM = 128
 FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 8, "raster_bwd": 16}
 ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 
-# DRAM bytes (read + write) per launch of each rasteriser, per workload, from
-# one ncu capture of that workload's bench step (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid while the rasteriser sources hash to the
-# value they had then (null otherwise).
+# DRAM bytes (read + write) per launch of each rasteriser configuration, per
+# workload, from ncu captures of that workload's bench step
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
+# the rasteriser sources hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": None,
-    "per_workload": {},
+    "source_sha256_16": "2e868df7171ce409",
+    "per_workload": {  # workload -> {configuration name: bytes per launch}
+        "A5": {
+            "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first": 1532016000.0,
+            "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first": 1524705920.0,
+            "1 lane per record, 128-record warp windows": 3881282560.0,
+            "1 lane per record, 128-record warp windows, persistent longest-first": 4823263872.0,
+        },
+    },
 }
 
 
@@ -113,6 +121,9 @@ def parse():
     ap.add_argument("--secondary", default="A2",
                     help="comma-separated workloads also timed on the device (N=1 only; '' for none)")
     ap.add_argument("--no-parity", action="store_true", help="skip the sampled check against the oracle")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="images per step instead of the workload's own (a smaller case of the same "
+                         "workload, e.g. for a profiler capture)")
     ap.add_argument("--raster-config", default=None,
                     help="'F,B': use forward / backward rasteriser configurations F, B (indices of "
                          "binding.raster_configs()) instead of the autotuner's choice")
@@ -501,6 +512,8 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     w = syn.WORKLOADS[args.workload]
+    if args.batch:
+        w = dataclasses.replace(w, B=args.batch)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
 
@@ -676,9 +689,10 @@ def main():
     peak = sms * per_clk * mhz * 1e6 / 1e9  # Gpair/s
     peak_sfu = sms * EX2_PER_CLK_PER_SM * mhz * 1e6 / 1e9
     achieved = kept / (per_stage[dom] / 1e3) / 1e9
-    cap = CAPTURED_TRAFFIC["per_workload"].get(w.name) \
-        if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] else None
-    traffic = cap[dom] if cap else None
+    cap = CAPTURED_TRAFFIC["per_workload"].get(w.name, {}) \
+        if raster_source_hash() == CAPTURED_TRAFFIC["source_sha256_16"] and not args.batch else {}
+    cfg_name = {"raster_fwd": raster_cfg["forward"], "raster_bwd": raster_cfg["backward"]}
+    traffic = cap.get(cfg_name[dom])
     other = "raster_bwd" if dom == "raster_fwd" else "raster_fwd"
     o_peak = sms * min(FP32_PER_CLK_PER_SM / FP32_OPS_PER_KEPT_PAIR[other], EX2_PER_CLK_PER_SM) * mhz * 1e6 / 1e9
     o_ach = kept / (per_stage[other] / 1e3) / 1e9
@@ -693,7 +707,7 @@ def main():
             "other_rasteriser": {"kernel": other, "achieved": o_ach, "peak": o_peak, "frac": o_ach / o_peak,
                                  "ops_per_kept_pair": FP32_OPS_PER_KEPT_PAIR[other],
                                  "frac_all_fp32_ops": o_ach / all_ops_peak(other),
-                                 "traffic": cap[other] if cap else None},
+                                 "traffic": cap.get(cfg_name[other])},
             "peak_note": f"{sms} SMs x min({FP32_PER_CLK_PER_SM} FP32 lanes / {ops} FMA-pipe ops per kept "
                          f"pair, {EX2_PER_CLK_PER_SM} ex2) per clock x {mhz:.0f} MHz median SM clock under load",
             "sfu_only": {"peak": peak_sfu, "frac": achieved / peak_sfu,

@@ -472,15 +472,38 @@ __global__ void __launch_bounds__(32 * kScanWarps) tile_scan_cols_kernel(
   uint32_t *col = tcnt + (int64_t)b * nch * T + t;
   const int per = (nch + kScanWarps - 1) / kScanWarps;
   const int c0 = min(nch, warp * per), c1 = min(nch, c0 + per);
+  // eight loads in flight per lane in both passes (the chunk walk is
+  // otherwise one dependent load per step)
+  constexpr int kU = 8;
   uint32_t sum = 0;
-  if (act)
-    for (int c = c0; c < c1; ++c) sum += col[(int64_t)c * T];
+  if (act) {
+    int c = c0;
+    for (; c + kU <= c1; c += kU) {
+      uint32_t v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) v[u] = col[(int64_t)(c + u) * T];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) sum += v[u];
+    }
+    for (; c < c1; ++c) sum += col[(int64_t)c * T];
+  }
   part[warp][lane] = sum;
   __syncthreads();
   uint32_t run = 0;
   for (int w = 0; w < warp; ++w) run += part[w][lane];
   if (act) {
-    for (int c = c0; c < c1; ++c) {
+    int c = c0;
+    for (; c + kU <= c1; c += kU) {
+      uint32_t v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) v[u] = col[(int64_t)(c + u) * T];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        col[(int64_t)(c + u) * T] = run;
+        run += v[u];
+      }
+    }
+    for (; c < c1; ++c) {
       const uint32_t v = col[(int64_t)c * T];
       col[(int64_t)c * T] = run;
       run += v;
@@ -548,64 +571,80 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
 // their tile; a hit's place in its tile's list is the tile's start, plus the
 // chunk's offset for that tile, plus the number of lower bits set (so the
 // list keeps the chunk's depth order).  Beside the Gaussian's index the
-// entry stores its 4x4-block mask.  The chunk's Gaussian indices and the
-// list position of every tile it hits are staged first, so that each hit
-// costs one load of its own and two stores.
+// entry stores its 4x4-block mask.  Only the tiles the chunk hits are
+// touched: each hit clears its own tile's bitmap words first (a chunk hits
+// a few hundred of the image's tiles at most, and large images have
+// thousands), and looks up its own tile's list base.
 __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     const uint32_t *__restrict__ perm, int64_t M, int d, int nch,
     const uint32_t *__restrict__ tcnt, const int64_t *__restrict__ tile_start, BinScratch bs) {
   // bitmaps word-major, [8][T]: a warp's hits are mostly one Gaussian's
-  // neighbouring tiles, which then fall in neighbouring banks; then the
-  // int64 list base of each tile [T]
+  // neighbouring tiles, which then fall in neighbouring banks
   extern __shared__ __align__(16) uint32_t bm[];
   __shared__ uint32_t sj[kChunkT];   // Gaussian index of each slot
   const int c = blockIdx.x, b = blockIdx.y;
   const int nt = d / kTile, T = nt * nt;
-  int64_t *tb = reinterpret_cast<int64_t *>(bm + T * 8);
-  for (int i = threadIdx.x; i < T * 8; i += blockDim.x) bm[i] = 0;
   const int64_t r0 = (int64_t)c * kChunkT;
   if (r0 + threadIdx.x < M)
     sj[threadIdx.x] = perm ? perm[(int64_t)b * M + r0 + threadIdx.x] : (uint32_t)(r0 + threadIdx.x);
   const int64_t hb = bs.chunk_base[(int64_t)b * nch + c];
   const int64_t hn = min((int64_t)bs.chunk_n[(int64_t)b * nch + c], max(bs.cap - hb, (int64_t)0));
   const int H = (int)hn;
-  __syncthreads();
   const uint64_t *hr = bs.hits + hb;
-  for (int i = threadIdx.x; i < H; i += blockDim.x) {
-    const uint64_t h = hr[i];
+  // the first kHold hits of each thread (i = thread + k * kChunkT) stay in
+  // registers across the three phases (the index k is a compile-time
+  // constant of an unrolled loop, so the array never leaves registers); a
+  // chunk with more hits reads the rest again from global memory
+  constexpr int kHold = 4;
+  uint64_t hold[kHold];
+#pragma unroll
+  for (int k = 0; k < kHold; ++k) {
+    const int i = threadIdx.x + k * kChunkT;
+    hold[k] = i < H ? hr[i] : 0ull;
+  }
+  auto zero_tile = [&](uint64_t h) {
+    const int t = (int)((h >> 8) & 0xffffu);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bm[q * T + t] = 0u;
+  };
+  auto set_bit = [&](uint64_t h) {
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
     atomicOr(&bm[(o >> 5) * T + t], 1u << (o & 31));
-  }
-  __syncthreads();
-  // list base of every tile the chunk hits: the tile's start plus the
-  // chunk's offset in it
+  };
+  // list base of a hit's tile: the tile's start plus the chunk's offset in it
   const uint32_t *coff = tcnt + ((int64_t)b * nch + c) * T;
-  for (int i = threadIdx.x; i < T; i += blockDim.x) {
-    uint32_t any = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) any |= bm[q * T + i];
-    if (any) tb[i] = tile_start[(int64_t)b * T + i] + coff[i];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < H; i += blockDim.x) {
-    const uint64_t h = hr[i];
+  auto place = [&](uint64_t h) {
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
     const uint32_t *bw = bm + t;
     const int word = o >> 5;
     uint32_t rank = __popc(bw[word * T] & ((1u << (o & 31)) - 1u));
     for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk * T]);
-    const int64_t pos = tb[t] + rank;
+    const int64_t pos = tile_start[(int64_t)b * T + t] + coff[t] + rank;
     if (pos < bs.cap) {
       bs.list[pos] = sj[o];
       bs.lmask[pos] = (uint16_t)(h >> 24);
     }
-  }
+  };
+#pragma unroll
+  for (int k = 0; k < kHold; ++k)
+    if (threadIdx.x + k * kChunkT < H) zero_tile(hold[k]);
+  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) zero_tile(hr[i]);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kHold; ++k)
+    if (threadIdx.x + k * kChunkT < H) set_bit(hold[k]);
+  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) set_bit(hr[i]);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kHold; ++k)
+    if (threadIdx.x + k * kChunkT < H) place(hold[k]);
+  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) place(hr[i]);
 }
 
-// Bitmaps (8 words, word-major) and list base (8 bytes) per tile.
+// Bitmaps (8 words per tile, word-major).
 static int tile_smem_bytes(int d) {
   int nt = d / kTile;
-  return nt * nt * (8 * (int)sizeof(uint32_t) + (int)sizeof(int64_t));
+  return nt * nt * 8 * (int)sizeof(uint32_t);
 }
 
 // The dynamic shared memory of both tile kernels (bitmaps, counters) is

@@ -628,6 +628,79 @@ cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
                               kept, order, next_tile, st);
 }
 
+// The six moments of w = g * value over pixel rows row0 .. row0 + kRows - 1
+// of block k of the tile at (x0, y0) for one record (centre A.x, A.y and
+// exponent terms A.z, A.w, cc, l2A), added to the running totals
+// (n0, n1), (n2, n3), (n4, n5):
+//   n0 = sum w, n1 = sum w dx, n2 = sum w dy,
+//   n3 = sum w (dx^2 - S^xx), n4 = sum w (dx dy - S^xy), n5 = sum w (dy^2 - S^yy)
+// (per row: the sums of w, w dx, w dx^2 in packed float pairs, weighted by
+// dy; the second moments taken about S^ per block).  sg is the g tile,
+// [pixel row in block][block].
+template <int kRows>
+__device__ __forceinline__ void block_moments(const float4 (*__restrict__ sg)[16], int k, int x0,
+                                              int y0, int row0, const float4 &A, float cc,
+                                              float l2A, float l2tau, float sxx, float sxy,
+                                              float syy, float2 &s01, float2 &s23, float2 &s45) {
+  const float2 ca2 = f2(A.z);
+  const float cb = A.w;
+  const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
+  const float fy = (float)(y0 + 4 * (k >> 2) + row0) - A.y;
+  const float2 dx01 = make_float2(fx, fx + 1.f);
+  const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
+  const float2 dxx01 = mul2(dx01, dx01), dxx23 = mul2(dx23, dx23);
+  // this block's rows: sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2
+  float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
+#pragma unroll
+  for (int rr = 0; rr < kRows; ++rr) {
+    const float dy = fy + (float)rr;
+    const float2 bdy = f2(cb * dy);
+    const float2 cdy = f2(fmaf(cc * dy, dy, l2A));
+    // e = (ca dx + cb dy) dx + cc dy^2 + l2A, as in the forward's terms
+    const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
+    const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
+    const float4 g4 = sg[row0 + rr][k];
+    // w = g * value on kept pairs (value > tau), zero elsewhere
+    const float2 gm01 = mul2(make_float2(g4.x, g4.y),
+                             make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
+    const float2 gm23 = mul2(make_float2(g4.z, g4.w),
+                             make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)));
+    const float2 w01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
+    const float2 w23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
+    // the row's sums of w, w dx and w dx^2, then weighted by dy
+    const float2 s0 = add2(w01, w23);
+    const float2 s1 = fma2(w23, dx23, mul2(w01, dx01));
+    const float2 s2 = fma2(w23, dxx23, mul2(w01, dxx01));
+    const float r0 = s0.x + s0.y, r1 = s1.x + s1.y, r2 = s2.x + s2.y;
+    m0 += r0;
+    m1 += r1;
+    m3 += r2;
+    m2 = fmaf(r0, dy, m2);
+    m4 = fmaf(r1, dy, m4);
+    m5 = fmaf(r0 * dy, dy, m5);
+  }
+  // second moments about S^, then into the totals
+  m3 = fmaf(-sxx, m0, m3);
+  m4 = fmaf(-sxy, m0, m4);
+  m5 = fmaf(-syy, m0, m5);
+  s01 = add2(s01, make_float2(m0, m1));
+  s23 = add2(s23, make_float2(m2, m3));
+  s45 = add2(s45, make_float2(m4, m5));
+}
+
+// S^ of a record: the inverse of the conic its exponent evaluates,
+// C = -2 ln2 [[ca, cb/2], [cb/2, cc]], so S^ = log2(e) / D
+// [[-2 cc, cb], [cb, -2 ca]] with D = 4 ca cc - cb^2 (cb^2 split exactly, so
+// D keeps its digits for elongated Gaussians).
+__device__ __forceinline__ void record_cov(float ca, float cb, float cc, float &sxx, float &sxy,
+                                           float &syy) {
+  const float cb2 = cb * cb, cb2l = fmaf(cb, cb, -cb2);
+  const float rD = kLog2e / (fmaf(4.f * ca, cc, -cb2) - cb2l);
+  sxx = -2.f * cc * rD;
+  sxy = cb * rD;
+  syy = -2.f * ca * rD;
+}
+
 // kLpr lanes share one record (lane q of the group takes pixel rows
 // q * 4 / kLpr .. of every block of the record), so a round runs 32 / kLpr
 // records of neighbouring block counts; a warp window holds 32 * kPer
@@ -750,61 +823,13 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       if (!mk) continue;  // the whole group skips: the counts are sorted
       const float4 A = sa[warp][slot];
       const float2 Bv = sb[warp][slot];
-      const float2 ca2 = f2(A.z);
-      const float cb = A.w, cc = Bv.x, l2A = Bv.y;
-      // S^ of the record: the inverse of the conic its exponent evaluates,
-      // C = -2 ln2 [[ca, cb/2], [cb/2, cc]], so S^ = log2(e) / D
-      // [[-2 cc, cb], [cb, -2 ca]] with D = 4 ca cc - cb^2 (cb^2 split
-      // exactly, so D keeps its digits for elongated Gaussians)
-      const float cb2 = cb * cb, cb2l = fmaf(cb, cb, -cb2);
-      const float rD = kLog2e / (fmaf(4.f * A.z, cc, -cb2) - cb2l);
-      const float sxx = -2.f * cc * rD, sxy = cb * rD, syy = -2.f * A.z * rD;
+      const float cc = Bv.x, l2A = Bv.y;
+      float sxx, sxy, syy;
+      record_cov(A.z, A.w, cc, sxx, sxy, syy);
       float2 s01 = make_float2(0.f, 0.f), s23 = s01, s45 = s01;  // lane totals: (n0, n1), (n2, n3), (n4, n5)
-      for (unsigned mm = mk; mm; mm &= mm - 1) {
-        const int k = __ffs(mm) - 1;
-        const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
-        const float fy = (float)(y0 + 4 * (k >> 2) + row0) - A.y;
-        const float2 dx01 = make_float2(fx, fx + 1.f);
-        const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
-        const float2 dxx01 = mul2(dx01, dx01), dxx23 = mul2(dx23, dx23);
-        // this block's rows: sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
-#pragma unroll
-        for (int rr = 0; rr < kRows; ++rr) {
-          const float dy = fy + (float)rr;
-          const float2 bdy = f2(cb * dy);
-          const float2 cdy = f2(fmaf(cc * dy, dy, l2A));
-          // e = (ca dx + cb dy) dx + cc dy^2 + l2A, as in the forward's terms
-          const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
-          const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
-          const float4 g4 = sg[row0 + rr][k];
-          // w = g * value on kept pairs (value > tau), zero elsewhere
-          const float2 gm01 = mul2(make_float2(g4.x, g4.y),
-                                   make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
-          const float2 gm23 = mul2(make_float2(g4.z, g4.w),
-                                   make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)));
-          const float2 w01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
-          const float2 w23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
-          // the row's sums of w, w dx and w dx^2, then weighted by dy
-          const float2 s0 = add2(w01, w23);
-          const float2 s1 = fma2(w23, dx23, mul2(w01, dx01));
-          const float2 s2 = fma2(w23, dxx23, mul2(w01, dxx01));
-          const float r0 = s0.x + s0.y, r1 = s1.x + s1.y, r2 = s2.x + s2.y;
-          m0 += r0;
-          m1 += r1;
-          m3 += r2;
-          m2 = fmaf(r0, dy, m2);
-          m4 = fmaf(r1, dy, m4);
-          m5 = fmaf(r0 * dy, dy, m5);
-        }
-        // second moments about S^, then into the lane's totals
-        m3 = fmaf(-sxx, m0, m3);
-        m4 = fmaf(-sxy, m0, m4);
-        m5 = fmaf(-syy, m0, m5);
-        s01 = add2(s01, make_float2(m0, m1));
-        s23 = add2(s23, make_float2(m2, m3));
-        s45 = add2(s45, make_float2(m4, m5));
-      }
+      for (unsigned mm = mk; mm; mm &= mm - 1)
+        block_moments<kRows>(sg, __ffs(mm) - 1, x0, y0, row0, A, cc, l2A, l2tau, sxx, sxy, syy, s01,
+                             s23, s45);
       float m0 = s01.x, m1 = s01.y, m2 = s23.x, m3 = s23.y, m4 = s45.x, m5 = s45.y;
 #pragma unroll
       for (int o = 1; o < kLpr; o <<= 1) {
