@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
 // blocks in proportion to their item counts (every non-empty block gets at
 // least one thread: thread range [T_k, T_k+1) with T_k = (non-empty blocks
 // before k) + floor((128 - non-empty) * start_k / N)), and a block's threads
-// split its items evenly.  A run never leaves its block, so each thread ends
+// take its items interleaved.  A thread never leaves its block, so each thread ends
 // the window with one partial image of its block (16 pixels), and each pixel
 // sums the partials of its block's thread range in thread order (runs in
 // list order), then joins its running sum with Kahan compensation.  The
@@ -426,11 +426,15 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
       if (tk > 0 && tid < tf[k + 1]) {
-        const int L = ps[k + 1] - ps[k], j = tid - t0;
-        const int lo = ps[k] + (j * L) / tk, hi = ps[k] + ((j + 1) * L) / tk;
+        const int j = tid - t0;
+        // the block's threads take its items interleaved (thread j: items
+        // j, j + tk, ...), each in list order; at every step they read
+        // neighbouring items, whose slots ascend, which spreads the record
+        // gathers over the banks better than contiguous runs did
+        const int L = ps[k + 1] - ps[k];
         const float X0 = (float)(x0 + 4 * (k & 3)), Y0 = (float)(y0 + 4 * (k >> 2));
         const float2 xs01 = make_float2(X0, X0 + 1.f), xs23 = make_float2(X0 + 2.f, X0 + 3.f);
-        for (int i = lo; i < hi; ++i) {
+        for (int i = ps[k] + j; i < ps[k] + L; i += tk) {
           const int slot = flat[i];
           const float4 A = sa[slot];
           const float2 Bv = sb[slot];
