@@ -70,7 +70,7 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # DRAM bytes (read + write) per launch of each rasteriser configuration, per
 # workload, from ncu captures of that workload's bench step
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
-# the rasteriser sources hash to the value they had then (null otherwise).
+# the library's CUDA sources hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
     "source_sha256_16": "2e868df7171ce409",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
@@ -97,17 +97,17 @@ HBM_PEAK_GBS, HBM_PEAK_NOTE = _hbm_peak()
 
 
 def raster_source_hash() -> str:
-    """Hash of the rasterisers' source: gem_raster.cu and the device helpers
-    and types of gem_internal.cuh (the part before its launcher list)."""
+    """Hash of every CUDA source of the library: the rasterisers' traffic
+    depends on their own code and on the memory order of the records the
+    preprocess writes."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_25075_gb300", "csrc")
-    with open(os.path.join(csrc, "gem_raster.cu"), "rb") as fh:
-        h.update(fh.read())
-    with open(os.path.join(csrc, "gem_internal.cuh"), "rb") as fh:
-        head = fh.read()
-    h.update(head.split(b"// ---- launchers", 1)[0])
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 

@@ -71,7 +71,8 @@ typedef struct gem_config {
   int64_t max_M;     /* largest Gaussian count any call will pass, 1..2^24                    */
   int64_t max_pairs; /* capacity of the (image, tile, Gaussian) lists; 0 picks 16*max_B*max_M */
   int32_t zsort;     /* 1: accumulate each pixel from the lowest depth z' to the highest      */
-                     /*    (Sec. 3.2); 0: in Gaussian index order.  Changes rounding only.    */
+                     /*    (Sec. 3.2); 0: in slot order (see gem_project).  Changes        */
+                     /*    rounding only.                                                  */
   int32_t no_rotation; /* 1: every Gaussian uses R_j = I and q is ignored (its gradient is 0); */
                        /*    the "No Rotation" ablation of Sec. 4 (Design Choices, Table 4)  */
   int32_t isotropic;   /* 1: S_j = s_j I with s_j = the first scale entry; the other two are   */
@@ -122,8 +123,13 @@ int gem_status(gem_ctx *ctx);
  *   params [M][11], R [B][3][3], t [B][2]  ->  proj [B][d][d].
  * Preprocesses every (view, Gaussian), bins the kept pairs into 16 x 16
  * pixel tiles (each tile's Gaussians in ascending depth when zsort = 1) and
- * rasterises.  The context keeps the bins and the pointers params, R, t for
- * gem_project_backward: they must stay valid and unchanged until then.
+ * rasterises.  Internally the Gaussians are held in slot order, a stable
+ * sort by the 3D Morton key of their means (5 bits per axis over the box of
+ * side d apix centred on the origin), so that Gaussians close in space are
+ * close in memory; Gaussians with equal 16-bit depth keys accumulate in
+ * slot order.  Every output is in the caller's Gaussian order.  The context
+ * keeps the bins and the pointers params, R, t for gem_project_backward:
+ * they must stay valid and unchanged until then.
  * Errors: GEM_EINVAL (M < 1 or > max_M, B < 1 or > max_B, null pointer). */
 int gem_project(gem_ctx *ctx, const float *params, int64_t M, int32_t B, const float *R,
                 const float *t, float *proj);

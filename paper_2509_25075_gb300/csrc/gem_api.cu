@@ -28,8 +28,12 @@ struct gem_ctx {
   float l2tau = 0.f;
   FftPlan plan{};
   // scratch
-  GaussPrep *gp = nullptr;
-  Rec *rec = nullptr;
+  GaussPrep *gp = nullptr;       // [max_M] by slot
+  Rec *rec = nullptr;            // [max_B][max_M] by view, slot
+  uint32_t *slot_gauss = nullptr;  // [max_M] Gaussian of each slot (3D Morton order)
+  uint32_t *gauss_slot = nullptr;  // [max_M] slot of each Gaussian
+  float *psort = nullptr;          // [max_M][11] parameters by slot
+  uint16_t *mkey = nullptr;        // [max_M] Morton keys
 
   BinScratch bin{};
   double *mom = nullptr;   // [max_B][max_M][6] moments of the raster backward
@@ -259,7 +263,9 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
   const size_t BM = (size_t)g.max_B * (size_t)g.max_M;
   const size_t nchD = bin_chunks_depth(g.max_M), nchT = bin_chunks_tiles(g.max_M);
   c->nbg = g.max_B < 16 ? g.max_B : 16;
-  bool ok = alloc(c, &c->gp, g.max_M) && alloc(c, &c->rec, BM) && alloc(c, &c->bin.key, BM) &&
+  bool ok = alloc(c, &c->gp, g.max_M) && alloc(c, &c->slot_gauss, g.max_M) &&
+            alloc(c, &c->gauss_slot, g.max_M) && alloc(c, &c->psort, (size_t)g.max_M * kNpar) &&
+            alloc(c, &c->mkey, g.max_M) && alloc(c, &c->rec, BM) && alloc(c, &c->bin.key, BM) &&
             alloc(c, &c->bin.packed, BM) && alloc(c, &c->bin.perm, BM) &&
             alloc(c, &c->bin.dcnt, (size_t)g.max_B * nchD * 256) &&
             alloc(c, &c->bin.tcnt, (size_t)g.max_B * nchT * c->T) &&
@@ -370,10 +376,17 @@ static int check_project_args(gem_ctx *c, const float *params, int64_t M, int32_
 
 static int prep(gem_ctx *c, const float *params, int64_t M, int32_t B, const float *R,
                 const float *t) {
-  StageScope sc(c, GEM_STAGE_PREP, 2);
+  StageScope sc(c, GEM_STAGE_PREP, 9);
   cudaError_t e;
   const gem_config &g = c->cfg;
-  if ((e = launch_gauss_prep(params, M, g.norm_mode, shape_flags(g), c->gp, c->stream)) != cudaSuccess)
+  // slot order: a stable sort of the Gaussians by the 3D Morton key of their
+  // means (the binning's depth-pass scratch is free until the binning)
+  if ((e = launch_morton_key(params, M, (float)g.d * g.apix, c->mkey, c->stream)) != cudaSuccess ||
+      (e = launch_sort16(c->mkey, M, 1, c->bin.dcnt, c->bin.packed, c->slot_gauss, c->stream)) !=
+          cudaSuccess)
+    return cuda_fail(c, e, "slot order");
+  if ((e = launch_gauss_prep(params, c->slot_gauss, M, g.norm_mode, shape_flags(g), c->gp,
+                             c->psort, c->gauss_slot, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "gauss_prep");
   // depth keys span [-d apix, d apix]: the half-diagonal of the box is shorter
   const float zrange = (float)g.d * g.apix;
@@ -483,7 +496,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
   StageScope sc(c, GEM_STAGE_PREP_BWD, 2);
-  if ((e = launch_prep_bwd(c->params, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode, shape_flags(g),
+  if ((e = launch_prep_bwd(c->psort, c->gauss_slot, c->gp, c->M, c->B, c->R, c->t, g.apix, g.d, g.norm_mode, shape_flags(g),
                            c->mom, c->part, c->nbg, grad, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "prep_bwd");
   c->mom_clean = true;
@@ -600,10 +613,14 @@ int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t li
                                 (long long)list_cap, (long long)n);
   cudaError_t e;
   size_t ts = ((size_t)c->bins_B * c->T + 1) * sizeof(int64_t);
+  // the lists of a projection hold slots: map them to Gaussian indices
   if ((e = cudaMemcpy(tile_start, c->bin.tile_start, ts, cudaMemcpyDeviceToDevice)) !=
           cudaSuccess ||
-      (e = cudaMemcpy(list, c->bin.list, (size_t)n * sizeof(uint32_t),
-                      cudaMemcpyDeviceToDevice)) != cudaSuccess)
+      (e = c->bins_of_proj
+               ? launch_map_slots(c->bin.list, c->slot_gauss, n, list, c->stream)
+               : cudaMemcpyAsync(list, c->bin.list, (size_t)n * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "inspect copy");
   return GEM_OK;
 }
@@ -611,7 +628,7 @@ int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t li
 int gem_inspect_records(gem_ctx *c, float *out) {
   if (!c || !out) return GEM_EINVAL;
   if (!c->have_proj) return fail(c, GEM_ESTATE, "no projection yet");
-  cudaError_t e = launch_inspect_records(c->rec, c->gp, c->M, c->B, c->R, c->t, c->cfg.apix,
+  cudaError_t e = launch_inspect_records(c->rec, c->gp, c->slot_gauss, c->M, c->B, c->R, c->t, c->cfg.apix,
                                          c->cfg.d, out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "inspect records");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess)

@@ -57,27 +57,66 @@ __global__ void __launch_bounds__(kDThreads) digit_count_kernel(
 
 // Turn cnt[b][c][bin] into the output offset (within image b) of the first
 // element of chunk c with that digit: per bin, exclusive scan over chunks,
-// plus the number of elements of image b with a smaller digit.
-__global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *__restrict__ cnt, int nch) {
-  int b = blockIdx.x, bin = threadIdx.x;
+// plus the number of elements of image b with a smaller digit.  Thread
+// (g, bin) takes the g-th quarter of the chunks of its bin, 8 loads in
+// flight: a pass of range sums, the ranges' and bins' prefixes, a pass that
+// writes the offsets.
+constexpr int kScanGroups = 4;
+__global__ void __launch_bounds__(256 * kScanGroups) digit_scan_kernel(uint32_t *__restrict__ cnt,
+                                                                        int nch) {
+  __shared__ uint32_t part[kScanGroups][256];
+  __shared__ uint32_t wsum[8];
+  const int b = blockIdx.x, bin = threadIdx.x & 255, g = threadIdx.x >> 8;
+  const int per = (nch + kScanGroups - 1) / kScanGroups;
+  const int c0 = min(nch, g * per), c1 = min(nch, c0 + per);
   uint32_t *col = cnt + (int64_t)b * nch * 256 + bin;
-  uint32_t run = 0;
-  for (int c = 0; c < nch; ++c) {
-    uint32_t v = col[(int64_t)c * 256];
+  uint32_t sum = 0;
+  int c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = col[(int64_t)(c + k) * 256];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += v[k];
+  }
+  for (; c < c1; ++c) sum += col[(int64_t)c * 256];
+  part[g][bin] = sum;
+  __syncthreads();
+  uint32_t before = 0, tot = 0;
+#pragma unroll
+  for (int q = 0; q < kScanGroups; ++q) {
+    const uint32_t v = part[q][bin];
+    if (q < g) before += v;
+    tot += v;
+  }
+  // exclusive prefix of the bin totals (group 0's 8 warps hold bins 0..255)
+  uint32_t incl = tot;
+  const int lane = threadIdx.x & 31, warp = bin >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (g == 0 && lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t run = incl - tot + before;
+  for (int w = 0; w < warp; ++w) run += wsum[w];
+  c = c0;
+  for (; c + 8 <= c1; c += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = col[(int64_t)(c + k) * 256];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      col[(int64_t)(c + k) * 256] = run;
+      run += v[k];
+    }
+  }
+  for (; c < c1; ++c) {
+    const uint32_t v = col[(int64_t)c * 256];
     col[(int64_t)c * 256] = run;
     run += v;
   }
-  __shared__ uint32_t tot[256];
-  tot[bin] = run;
-  __syncthreads();
-  for (int off = 1; off < 256; off <<= 1) {
-    uint32_t v = bin >= off ? tot[bin - off] : 0;
-    __syncthreads();
-    tot[bin] += v;
-    __syncthreads();
-  }
-  uint32_t base = tot[bin] - run;
-  for (int c = 0; c < nch; ++c) col[(int64_t)c * 256] += base;
 }
 
 // Lanes of the warp holding the same kBits-bit value: one ballot per bit
@@ -659,22 +698,41 @@ cudaError_t bin_configure(int d) {
                               (d / kTile) * (d / kTile) * (int)sizeof(uint32_t));
 }
 
+cudaError_t launch_sort16(const uint16_t *key, int64_t M, int B, uint32_t *dcnt,
+                          uint32_t *packed, uint32_t *perm, cudaStream_t st) {
+  int nch = (int)bin_chunks_depth(M);
+  dim3 g(nch, B);
+  // low byte, then high byte (LSD); ties keep index order
+  digit_count_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, dcnt);
+  digit_scan_kernel<<<B, 256 * kScanGroups, 0, st>>>(dcnt, nch);
+  digit_scatter_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, dcnt, packed);
+  digit_count_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, packed, M, nch, dcnt);
+  digit_scan_kernel<<<B, 256 * kScanGroups, 0, st>>>(dcnt, nch);
+  digit_scatter_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, packed, M, nch, dcnt, perm);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) map_slots_kernel(const uint32_t *__restrict__ list,
+                                                        const uint32_t *__restrict__ slot_gauss,
+                                                        int64_t n, uint32_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = slot_gauss[list[i]];
+}
+
+cudaError_t launch_map_slots(const uint32_t *list, const uint32_t *slot_gauss, int64_t n,
+                             uint32_t *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  map_slots_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(list, slot_gauss, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, int d,
                        float l2tau, int zsort, BinScratch &s, const uint32_t **perm_out,
                        cudaStream_t st) {
   cudaError_t e;
   const uint32_t *perm = nullptr;
   if (zsort) {
-    int nch = (int)bin_chunks_depth(M);
-    dim3 g(nch, B);
-    // low byte, then high byte (LSD); ties keep index order
-    digit_count_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, s.dcnt);
-    digit_scan_kernel<<<B, 256, 0, st>>>(s.dcnt, nch);
-    digit_scatter_kernel<0><<<g, kDThreads, 0, st>>>(key, nullptr, M, nch, s.dcnt, s.packed);
-    digit_count_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, s.packed, M, nch, s.dcnt);
-    digit_scan_kernel<<<B, 256, 0, st>>>(s.dcnt, nch);
-    digit_scatter_kernel<1><<<g, kDThreads, 0, st>>>(nullptr, s.packed, M, nch, s.dcnt, s.perm);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_sort16(key, M, B, s.dcnt, s.packed, s.perm, st)) != cudaSuccess) return e;
     perm = s.perm;
   }
   int nt = d / kTile, T = nt * nt;

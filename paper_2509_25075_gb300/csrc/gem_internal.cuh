@@ -147,19 +147,30 @@ __device__ __forceinline__ bool pixel_range(float c, float r, int d, int &lo, in
 constexpr int kNoRotation = 1;
 constexpr int kIsotropic = 2;
 
-cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, int shape,
-                              GaussPrep *gp, cudaStream_t st);
+// 15-bit 3D Morton key of every Gaussian's mean (cells of side / 32 over the
+// box of that side centred on the origin).
+cudaError_t launch_morton_key(const float *params, int64_t M, float side, uint16_t *key,
+                              cudaStream_t st);
+// slot_gauss: slot -> Gaussian (NULL: slot i is Gaussian i); gp is by slot.
+// psort [M][11] (the parameters by slot) and gauss_slot [M] (Gaussian ->
+// slot) are written unless psort is NULL.
+cudaError_t launch_gauss_prep(const float *params, const uint32_t *slot_gauss, int64_t M,
+                              int norm_mode, int shape, GaussPrep *gp, float *psort,
+                              uint32_t *gauss_slot, cudaStream_t st);
 cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
                              const float *t, float apix, int d, float l2tau, float zrange,
                              Rec *rec, uint16_t *key, cudaStream_t st);
 // Reads the float64 moments [B][M][6] and leaves them zero (the next
 // backward pass accumulates into them).
-cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
-                            const float *R, const float *t, float apix, int d, int norm_mode,
-                            int shape, double *mom, float *part, int nbg, float *grad,
-                            cudaStream_t st);
-cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t M, int B,
-                                   const float *R, const float *t, float apix, int d, float *out,
+// params (the slot-ordered copy), gp and the moments are by slot; grad
+// comes out by Gaussian through gauss_slot (NULL: slot i is Gaussian i).
+cudaError_t launch_prep_bwd(const float *params, const uint32_t *gauss_slot, const GaussPrep *gp,
+                            int64_t M, int B, const float *R, const float *t, float apix, int d,
+                            int norm_mode, int shape, double *mom, float *part, int nbg,
+                            float *grad, cudaStream_t st);
+cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp,
+                                   const uint32_t *slot_gauss, int64_t M, int B, const float *R,
+                                   const float *t, float apix, int d, float *out,
                                    cudaStream_t st);
 
 // gem_query.cu
@@ -252,6 +263,14 @@ struct BinScratch {
   int64_t cap;
   int *status;
 };
+// Stable sort of 16-bit keys [B][M] per row (two 8-bit counting passes,
+// ties in index order): perm[b][r] = index of rank r.  dcnt and packed are
+// scratch of the binning's sizes.
+cudaError_t launch_sort16(const uint16_t *key, int64_t M, int B, uint32_t *dcnt,
+                          uint32_t *packed, uint32_t *perm, cudaStream_t st);
+// Maps list entries (slots) to Gaussians: out[i] = slot_gauss[list[i]].
+cudaError_t launch_map_slots(const uint32_t *list, const uint32_t *slot_gauss, int64_t n,
+                             uint32_t *out, cudaStream_t st);
 // Returns the permutation used for binning in *perm_out (NULL: index order).
 cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, int d,
                        float l2tau, int zsort, BinScratch &s, const uint32_t **perm_out,

@@ -30,12 +30,73 @@ __device__ __forceinline__ Shape effective_shape(const float *th, int shape) {
   return e;
 }
 
-__global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict__ params,
-                                                         int64_t M, int norm_mode, int shape,
-                                                         GaussPrep *__restrict__ gp) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Slot order of the Gaussians: every per-Gaussian and per-(view, Gaussian)
+// array of the path (GaussPrep, records, depth keys, tile lists, moments) is
+// indexed by slot, and slot i holds Gaussian slot_gauss[i].  The slots
+// follow a 3D Morton order of the means (a stable sort by a 15-bit key:
+// 5 bits per axis over the box of side d apix centred on the origin, ties in
+// index order), so Gaussians close in space, which meet the same tiles in
+// every view, sit close in memory: the rasterisers' record gathers and the
+// backward's moment updates then share cache lines and stay in L2.  The
+// order changes no result beyond the summation order of Gaussians with equal
+// 16-bit depth keys.
+__device__ __forceinline__ unsigned morton_cell(float p, float inv_side) {
+  // separately rounded steps (no contraction), so the cell is reproducible
+  const float c = floorf(__fadd_rn(__fmul_rn(p, inv_side), 0.5f) * 32.f);
+  return (unsigned)fminf(fmaxf(c, 0.f), 31.f);  // NaN clamps to 0
+}
+
+__global__ void __launch_bounds__(256) morton_key_kernel(const float *__restrict__ params,
+                                                         int64_t M, float inv_side,
+                                                         uint16_t *__restrict__ key) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
   const float *th = params + j * kNpar;
+  const unsigned cx = morton_cell(th[0], inv_side), cy = morton_cell(th[1], inv_side),
+                 cz = morton_cell(th[2], inv_side);
+  unsigned k = 0;
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    k |= (((cx >> b) & 1u) << (3 * b)) | (((cy >> b) & 1u) << (3 * b + 1)) |
+         (((cz >> b) & 1u) << (3 * b + 2));
+  key[j] = (uint16_t)k;
+}
+
+cudaError_t launch_morton_key(const float *params, int64_t M, float side, uint16_t *key,
+                              cudaStream_t st) {
+  morton_key_kernel<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(params, M, 1.f / side, key);
+  return cudaGetLastError();
+}
+
+// Per slot i (Gaussian j = slot_gauss[i]): GaussPrep, the slot-ordered copy
+// of the parameters (read again by the preprocess backward) and the inverse
+// map gauss_slot[j] = i.  A warp gathers its 32 parameter rows through
+// shared memory, 32 consecutive words of the rows per load, and writes the
+// slot-ordered copy the same way.
+__global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict__ params,
+                                                         const uint32_t *__restrict__ slot_gauss,
+                                                         int64_t M, int norm_mode, int shape,
+                                                         GaussPrep *__restrict__ gp,
+                                                         float *__restrict__ psort,
+                                                         uint32_t *__restrict__ gauss_slot) {
+  __shared__ float rows[8][32 * kNpar];
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i0 = i - lane;  // the warp's first slot
+  const uint32_t j = i < M ? (slot_gauss ? slot_gauss[i] : (uint32_t)i) : 0u;
+  float *buf = rows[threadIdx.x >> 5];
+  for (int k = lane; k < 32 * kNpar; k += 32) {  // element k: row k / 11, entry k % 11
+    const int r = k / kNpar;
+    const uint32_t jr = __shfl_sync(0xffffffffu, j, r);
+    buf[k] = i0 + r < M ? params[(int64_t)jr * kNpar + (k - r * kNpar)] : 0.f;
+  }
+  __syncwarp();
+  if (psort)
+    for (int k = lane; k < 32 * kNpar; k += 32)
+      if (i0 + k / kNpar < M) psort[i0 * kNpar + k] = buf[k];
+  if (i >= M) return;
+  if (psort) gauss_slot[j] = (uint32_t)i;
+  const float *th = buf + lane * kNpar;
   float p0 = th[0], p1 = th[1], p2 = th[2];
   const Shape e = effective_shape(th, shape);
   float s0 = e.s0, s1 = e.s1, s2 = e.s2;
@@ -69,13 +130,15 @@ __global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict
     g.l2k = log2f(rho * sqrtf(two_pi) * fabsf(s0 * s1 * s2));
   g.valid = (ok && isfinite(g.l2k)) ? 1.f : 0.f;
   g.pad = 0.f;
-  gp[j] = g;
+  gp[i] = g;
 }
 
-cudaError_t launch_gauss_prep(const float *params, int64_t M, int norm_mode, int shape,
-                              GaussPrep *gp, cudaStream_t st) {
+cudaError_t launch_gauss_prep(const float *params, const uint32_t *slot_gauss, int64_t M,
+                              int norm_mode, int shape, GaussPrep *gp, float *psort,
+                              uint32_t *gauss_slot, cudaStream_t st) {
   int blocks = (int)((M + 255) / 256);
-  gauss_prep_kernel<<<blocks, 256, 0, st>>>(params, M, norm_mode, shape, gp);
+  gauss_prep_kernel<<<blocks, 256, 0, st>>>(params, slot_gauss, M, norm_mode, shape, gp, psort,
+                                            gauss_slot);
   return cudaGetLastError();
 }
 
@@ -136,20 +199,24 @@ cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float 
   return cudaGetLastError();
 }
 
+// Record of (view b, slot s) to out[b][Gaussian of slot s][8].
 __global__ void inspect_records_kernel(const Rec *__restrict__ rec,
-                                       const GaussPrep *__restrict__ gp, int64_t M, int64_t n,
-                                       const float *__restrict__ R, const float *__restrict__ t,
-                                       float apix, int d, float *__restrict__ out) {
+                                       const GaussPrep *__restrict__ gp,
+                                       const uint32_t *__restrict__ slot_gauss, int64_t M,
+                                       int64_t n, const float *__restrict__ R,
+                                       const float *__restrict__ t, float apix, int d,
+                                       float *__restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Rec r = rec[i];
   int b = (int)(i / M);
+  const int64_t sl = i - (int64_t)b * M;
   float Rl[9], tl[2];
   for (int k = 0; k < 9; ++k) Rl[k] = R[9 * b + k];
   tl[0] = t[2 * b];
   tl[1] = t[2 * b + 1];
-  const float depth = view_project(gp[i % M], Rl, tl, apix, d).depth;
-  float *o = out + i * 8;
+  const float depth = view_project(gp[sl], Rl, tl, apix, d).depth;
+  float *o = out + ((int64_t)b * M + (slot_gauss ? (int64_t)slot_gauss[sl] : sl)) * 8;
   bool valid = r.b.y > -INFINITY;
   o[0] = r.a.x;
   o[1] = r.a.y;
@@ -161,12 +228,13 @@ __global__ void inspect_records_kernel(const Rec *__restrict__ rec,
   o[7] = valid ? 1.f : 0.f;
 }
 
-cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp, int64_t M, int B,
-                                   const float *R, const float *t, float apix, int d, float *out,
+cudaError_t launch_inspect_records(const Rec *rec, const GaussPrep *gp,
+                                   const uint32_t *slot_gauss, int64_t M, int B, const float *R,
+                                   const float *t, float apix, int d, float *out,
                                    cudaStream_t st) {
   int64_t n = M * B;
-  inspect_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, gp, M, n, R, t, apix,
-                                                                      d, out);
+  inspect_records_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, gp, slot_gauss, M, n,
+                                                                      R, t, apix, d, out);
   return cudaGetLastError();
 }
 
@@ -198,15 +266,17 @@ struct Kahan {
 //   dL/drho = m0 / rho;  mode 1 adds m0 / s_k to dL/ds_k.
 // The view-independent part (Sigma -> s, q) is applied once per thread to
 // the summed dL/dSigma.
+// One thread per (slot, view group): params, gp, the moments and the
+// partial gradient part[group][slot][11] are all by slot.
 __global__ void __launch_bounds__(128) prep_bwd_kernel(
     const float *__restrict__ params, const GaussPrep *__restrict__ gp, int64_t M, int B,
-    const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode, int shape,
-    double *__restrict__ mom, int per_group, float *__restrict__ part) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float *__restrict__ R, const float *__restrict__ t, float apix, int d, int norm_mode,
+    int shape, double *__restrict__ mom, int per_group, float *__restrict__ part) {
+  const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int bg = blockIdx.y;
-  if (j >= M) return;
-  GaussPrep g = gp[j];
-  float *out = part + ((int64_t)bg * M + j) * kNpar;
+  if (sl >= M) return;
+  GaussPrep g = gp[sl];
+  float *out = part + ((int64_t)bg * M + sl) * kNpar;
   if (g.valid == 0.f) {
 #pragma unroll
     for (int m = 0; m < kNpar; ++m) out[m] = 0.f;
@@ -218,13 +288,13 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   // the next view's moments are loaded while this view's are used
   longlong2 na = make_longlong2(0, 0), nb = na, nc = na;
   if (b0 < b1) {
-    const longlong2 *m0p = reinterpret_cast<const longlong2 *>(mom + ((int64_t)b0 * M + j) * 6);
+    const longlong2 *m0p = reinterpret_cast<const longlong2 *>(mom + ((int64_t)b0 * M + sl) * 6);
     na = m0p[0];
     nb = m0p[1];
     nc = m0p[2];
   }
   for (int b = b0; b < b1; ++b) {
-    longlong2 *mm = reinterpret_cast<longlong2 *>(mom + ((int64_t)b * M + j) * 6);
+    longlong2 *mm = reinterpret_cast<longlong2 *>(mom + ((int64_t)b * M + sl) * 6);
     const longlong2 ma = na, mb = nb, mc = nc;
     if (b + 1 < b1) {
       const longlong2 *mn = mm + 3 * M;  // view b + 1
@@ -274,7 +344,7 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
     M0.add(m0);
   }
   // view-independent part: Sigma = Rq D Rq^T, D = diag(s^2)
-  const float *th = params + j * kNpar;
+  const float *th = params + sl * kNpar;
   const Shape e = effective_shape(th, shape);
   float s[3] = {e.s0, e.s1, e.s2};
   float qw = e.qw, qx = e.qx, qy = e.qy, qz = e.qz, rho = th[10];
@@ -337,20 +407,25 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   out[10] = M0.s / rho;
 }
 
+// grad[j][m] = sum over the view groups of part[group][slot of j][m].
 __global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__ part,
-                                                       int nbg, int64_t n,
+                                                       const uint32_t *__restrict__ gauss_slot,
+                                                       int nbg, int64_t M,
                                                        float *__restrict__ grad) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = M * kNpar;
   if (i >= n) return;
+  const int64_t j = i / kNpar, m = i - j * kNpar;
+  const int64_t src = (gauss_slot ? (int64_t)gauss_slot[j] : j) * kNpar + m;
   Kahan acc;
-  for (int g = 0; g < nbg; ++g) acc.add(part[(int64_t)g * n + i]);
+  for (int g = 0; g < nbg; ++g) acc.add(part[(int64_t)g * n + src]);
   grad[i] = acc.s;
 }
 
-cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M, int B,
-                            const float *R, const float *t, float apix, int d, int norm_mode,
-                            int shape, double *mom, float *part, int nbg, float *grad,
-                            cudaStream_t st) {
+cudaError_t launch_prep_bwd(const float *params, const uint32_t *gauss_slot, const GaussPrep *gp,
+                            int64_t M, int B, const float *R, const float *t, float apix, int d,
+                            int norm_mode, int shape, double *mom, float *part, int nbg,
+                            float *grad, cudaStream_t st) {
   // views per thread: enough (Gaussian, view-group) threads to fill the GPU
   // (about 2^20), and no more, so that the per-Gaussian reads, the
   // view-independent chain rule and the partial sums are shared by as many
@@ -365,7 +440,7 @@ cudaError_t launch_prep_bwd(const float *params, const GaussPrep *gp, int64_t M,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t n = M * kNpar;
-  grad_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, groups, n, grad);
+  grad_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, gauss_slot, groups, M, grad);
   return cudaGetLastError();
 }
 

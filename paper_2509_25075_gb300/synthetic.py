@@ -73,7 +73,7 @@ class Workload:
         return c
 
 
-# The five workloads of the hot-path contract.  A2 is the benchmark workload.
+# The five workloads of the hot-path contract.  A5 is the benchmark workload.
 WORKLOADS = {
     "A1": Workload("A1", d=64, M=2000, B=32, forward_only=True),
     "A2": Workload("A2", d=128, M=20000, B=256),

@@ -36,6 +36,24 @@ def context(w: syn.Workload, **kw):
                            norm_mode=kw.pop("norm_mode", w.norm_mode), **kw)
 
 
+def morton_keys(params, d, apix):
+    """15-bit 3D Morton key of every Gaussian's mean as the library defines
+    it (gem_project): cell floor((p / (d apix) + 1/2) 32) per axis, clamped
+    to 0..31 (each step rounded to float32), bits interleaved x, y, z from
+    bit 0."""
+    side = np.float32(np.float32(d) * np.float32(apix))
+    inv = np.float32(1.0) / side
+    p = np.asarray(params, dtype=np.float32)[:, :3]
+    with np.errstate(invalid="ignore"):
+        c = np.floor((p * inv + np.float32(0.5)) * np.float32(32.0))
+    c = np.clip(np.nan_to_num(c, nan=0.0), 0, 31).astype(np.int64)
+    key = np.zeros(len(p), dtype=np.int64)
+    for b in range(5):
+        for a in range(3):
+            key |= ((c[:, a] >> b) & 1) << (3 * b + a)
+    return key
+
+
 def borderline_pairs(inp, w, tau, norm_mode=0, rel=1e-5):
     """Number of (pixel, Gaussian) pairs whose FP64 value lies within
     rel * tau of tau, per image (brute force, small cases only)."""

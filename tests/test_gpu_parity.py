@@ -73,7 +73,8 @@ def test_records_match_oracle(w):
 def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
     """Each tile list holds every Gaussian with a pixel above tau in that tile
     (brute force), only Gaussians whose extent box meets the tile, no
-    duplicates, in ascending depth (zsort 1) or index order (zsort 0)."""
+    duplicates, in ascending depth (zsort 1) or slot order (zsort 0: the
+    3D Morton key of the mean, then the index)."""
     inp = gt.inputs(w)
     ctx, _, _ = _project(w, inp, zsort=zsort)
     ts, lst = ctx.gem_inspect_bins()
@@ -92,6 +93,7 @@ def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
     ry = np.sqrt(np.maximum(kappa, 0) * pre[..., 4]) / w.apix
     cx = pre[..., 0] / w.apix + w.d / 2
     cy = pre[..., 1] / w.apix + w.d / 2
+    mkey = gt.morton_keys(inp["params"], w.d, w.apix)
     assert ts[-1] == len(lst) == ctx.gem_pair_count()
     for b in range(w.B):
         for t in range(T):
@@ -109,7 +111,8 @@ def test_bins_cover_exact_pairs_and_are_ordered(w, zsort):
                 dz = np.diff(depth[b, ent])
                 assert np.all(dz >= -qstep), (b, t, dz.min())
             else:
-                assert np.all(np.diff(ent.astype(np.int64)) > 0)
+                order = mkey[ent].astype(np.int64) * w.M + ent
+                assert np.all(np.diff(order) > 0)
 
 
 @pytest.mark.parametrize("w", SMALL + LARGE, ids=lambda w: w.name)
