@@ -49,8 +49,17 @@ __global__ void __launch_bounds__(kDThreads) digit_count_kernel(
   __syncthreads();
   int64_t base = (int64_t)b * M + (int64_t)c * kChunkD;
   int64_t lim = min((int64_t)kChunkD, M - (int64_t)c * kChunkD);
-  for (int i = threadIdx.x; i < lim; i += kDThreads)
-    atomicAdd(&h[digit_of<kPass>(key, packed, base + i)], 1u);
+  // all of a thread's digits are loaded before the first increment
+  constexpr int kEach = kChunkD / kDThreads;
+  unsigned dg[kEach];
+#pragma unroll
+  for (int r = 0; r < kEach; ++r) {
+    const int i = threadIdx.x + r * kDThreads;
+    dg[r] = i < lim ? digit_of<kPass>(key, packed, base + i) : 256u;
+  }
+#pragma unroll
+  for (int r = 0; r < kEach; ++r)
+    if (dg[r] < 256u) atomicAdd(&h[dg[r]], 1u);
   __syncthreads();
   if (threadIdx.x < 256) cnt[((int64_t)b * nch + c) * 256 + threadIdx.x] = h[threadIdx.x];
 }
@@ -152,11 +161,31 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
   const int64_t cbase = (int64_t)c * kChunkD + warp * kPer;
   const int64_t ibase = (int64_t)b * M;
   const unsigned lt = (1u << lane) - 1u;
-  // per-warp digit counts (order does not matter here: plain increments)
-  for (int r = 0; r < kPer / 32; ++r) {
-    int64_t e = cbase + r * 32 + lane;
-    if (e < M) atomicAdd(&wc[warp][digit_of<kPass>(key, packed, ibase + e)], 1u);
+  // the warp's 256 elements, loaded once: digit and output word per round
+  constexpr int kRounds = kPer / 32;
+  int dig[kRounds];
+  uint32_t word[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const int64_t e = cbase + r * 32 + lane;
+    dig[r] = 256 + lane;  // tail lanes: a value no digit has
+    word[r] = 0;
+    if (e < M) {
+      if (kPass == 0) {
+        const uint16_t k = key[ibase + e];
+        dig[r] = k & 255;
+        word[r] = ((uint32_t)(k >> 8) << 24) | (uint32_t)e;
+      } else {
+        const uint32_t wd = packed[ibase + e];
+        dig[r] = (int)(wd >> 24);
+        word[r] = wd & 0xffffffu;
+      }
+    }
   }
+  // per-warp digit counts (order does not matter here: plain increments)
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r)
+    if (dig[r] < 256) atomicAdd(&wc[warp][dig[r]], 1u);
   __syncthreads();
   // exclusive prefix over warps, plus the chunk's offset
   if (threadIdx.x < 256) {
@@ -169,33 +198,20 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
     }
   }
   __syncthreads();
-  for (int r = 0; r < kPer / 32; ++r) {
-    int64_t e = cbase + r * 32 + lane;
-    bool act = e < M;
-    uint32_t word = 0;
-    int dig = 256 + lane;
-    if (act) {
-      if (kPass == 0) {
-        uint16_t k = key[ibase + e];
-        dig = k & 255;
-        word = ((uint32_t)(k >> 8) << 24) | (uint32_t)e;
-      } else {
-        word = packed[ibase + e];
-        dig = (int)(word >> 24);
-        word &= 0xffffffu;
-      }
-    }
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const bool act = cbase + r * 32 + lane < M;
     // a full round has no tail lanes, so the 8 digit bits decide alone;
     // the last round of a chunk also tells tail lanes (digit 256 + lane) apart
     const bool full = cbase + r * 32 + 31 < M;
-    unsigned peers = full ? same_value_lanes<8>(dig) : same_value_lanes<9>(dig);
+    unsigned peers = full ? same_value_lanes<8>(dig[r]) : same_value_lanes<9>(dig[r]);
     int leader = __ffs(peers) - 1;
     uint32_t pos = 0;
-    if (act) pos = wc[warp][dig] + __popc(peers & lt);
+    if (act) pos = wc[warp][dig[r]] + __popc(peers & lt);
     __syncwarp();
-    if (act && lane == leader) wc[warp][dig] += __popc(peers);
+    if (act && lane == leader) wc[warp][dig[r]] += __popc(peers);
     __syncwarp();
-    if (act && pos < (uint32_t)M) out[ibase + pos] = word;
+    if (act && pos < (uint32_t)M) out[ibase + pos] = word[r];
   }
 }
 
