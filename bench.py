@@ -70,7 +70,7 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # DRAM bytes (read + write) per launch of each rasteriser configuration, per
 # workload, from ncu captures of that workload's bench step
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
-# the library's CUDA sources hash to the value they had then (null otherwise).
+# the sources they depend on hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
     "source_sha256_16": "2e868df7171ce409",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
@@ -97,17 +97,16 @@ HBM_PEAK_GBS, HBM_PEAK_NOTE = _hbm_peak()
 
 
 def raster_source_hash() -> str:
-    """Hash of every CUDA source of the library: the rasterisers' traffic
-    depends on their own code and on the memory order of the records the
-    preprocess writes."""
+    """Hash of the sources the rasterisers' traffic depends on: their own
+    code, the preprocess (the memory order of the records it writes), the
+    binning (the order of the lists) and the shared device header."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_25075_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
+    for name in ("gem_bin.cu", "gem_internal.cuh", "gem_prep.cu", "gem_raster.cu"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 

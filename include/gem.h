@@ -363,8 +363,9 @@ int gem_activate(gem_ctx *ctx, int64_t M, const float *raw, float *params);
  *   B, proj, ctf, ctf_params, images, pred, dproj, loss_img, loss
  *                exactly as for gem_ctf_loss (caller-owned device memory);
  *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream).
- * Limits: B * d * d <= 1,048,576 and B * (d / 16 + 1) <= 65,536;
- * beyond them the call returns GEM_ECAPACITY and launches nothing.  Other bad
+ * Limits: B * d * d <= 1,048,576 and B * (P + 1) <= 65,536, P the loss
+ * partials per image (d / 16 or d / 8, so the first limit implies the
+ * second); beyond them the call returns GEM_ECAPACITY and launches nothing.  Other bad
  * arguments return GEM_EINVAL; CUDA failures GEM_ECUDA.
  * The first call on each device looks up the arrays' device addresses
  * (cudaGetSymbolAddress) and keeps them for the life of the process; make

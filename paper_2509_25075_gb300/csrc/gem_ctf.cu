@@ -15,12 +15,12 @@
 //
 // Three passes through a [B][d][d] complex buffer, stored transposed
 // (Z[b][kx][y]) so that every FFT runs on contiguous lines:
-//   pass 1: FFT along x of 16 rows of z, written transposed;
-//   pass 2: FFT along y of the lines kx and d - kx (8 pairs per CTA; the
+//   pass 1: FFT along x of kLines rows of z, written transposed;
+//   pass 2: FFT along y of the lines kx and d - kx (kLines / 2 pairs per CTA; the
 //           first CTA holds the self-paired lines 0 and d/2 in the slots
 //           of line 0's pair), CTF, loss, W, inverse FFT along y, written
 //           back in place;
-//   pass 3: inverse FFT along x of 16 rows, split into I_pred and dL/dI^.
+//   pass 3: inverse FFT along x of kLines rows, split into I_pred and dL/dI^.
 // FFTs are radix-4/2/3 Stockham transforms in shared memory (d = 2^a 3^b).
 #include <math.h>
 
@@ -53,19 +53,25 @@ bool fft_plan(int n, FftPlan &p) {
   return m == 1;
 }
 
-constexpr int kLines = 16;  // lines per CTA in every pass
+// Lines per CTA in every pass (kLines, a template parameter): 16 where two
+// line buffers of 16 lines leave room for four CTAs per SM, else 8 (large
+// images: more, smaller CTAs, so the last wave is short).
 constexpr int kCtfThreads = 256;
 
 // line stride in shared memory: one element of padding per line
 __host__ __device__ constexpr int ctf_ls(int d) { return d + 1; }
-static size_t ctf_smem(int d) { return (size_t)(2 * kLines * ctf_ls(d) + d) * sizeof(float2); }
+static size_t ctf_smem(int lines, int d) {
+  return (size_t)(2 * lines * ctf_ls(d) + d) * sizeof(float2);
+}
+static int ctf_lines(int d) { return ctf_smem(16, d) <= 56 * 1024 ? 16 : 8; }
 
 __device__ __forceinline__ void load_twiddles(float2 *tw_s, const float2 *__restrict__ tw,
                                               int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) tw_s[i] = tw[i];
 }
 
-// pass 1: rows y0..y0+15 of z = proj + i images -> FFT along x -> Z[b][kx][y]
+// pass 1: rows y0 .. y0 + kLines - 1 of z = proj + i images -> FFT along x -> Z[b][kx][y]
+template <int kLines>
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass1_kernel(
     const float *__restrict__ proj, const float *__restrict__ images, FftPlan pl,
     const float2 *__restrict__ tw, float2 *__restrict__ Z) {
@@ -188,19 +194,22 @@ __device__ __forceinline__ float ctf_at(const CtfConst &c, int sx, int sy) {
 __device__ __forceinline__ int signed_bin(int k, int d) { return k < d / 2 ? k : k - d; }
 
 // Line kx held in slot i of pass-2 CTA blk (see ctf_pass2_kernel).
+template <int kHalf>
 __device__ __forceinline__ int pass2_line(int blk, int i, int d) {
-  const int kx1 = 8 * blk + (i & 7);
-  return i < 8 ? kx1 : (kx1 == 0 ? d / 2 : d - kx1);
+  const int kx1 = kHalf * blk + (i & (kHalf - 1));
+  return i < kHalf ? kx1 : (kx1 == 0 ? d / 2 : d - kx1);
 }
 
-// pass 2: slots i < 8 hold the lines kx1 = 8 c + i (kx1 < d/2), slots 8 + i
-// their partners d - kx1; line 0 is its own partner, so its slot 8 holds
-// the other self-paired line, d/2.  d is a multiple of 16, so the d/16
-// CTAs of an image hold every line once.
+// pass 2: slots i < kHalf hold the lines kx1 = kHalf c + i (kx1 < d/2),
+// slots kHalf + i their partners d - kx1; line 0 is its own partner, so its
+// slot kHalf holds the other self-paired line, d/2.  d is a multiple of
+// kLines, so the d / kLines CTAs of an image hold every line once.
+template <int kLines>
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
     FftPlan pl, const float2 *__restrict__ tw, const float *__restrict__ ctf,
     const float *__restrict__ ctf_params, float apix, float2 *__restrict__ Z,
     double *__restrict__ lossp, int nblk) {
+  constexpr int kHalf = kLines / 2;  // line pairs per CTA
   extern __shared__ float2 sm[];
   __shared__ CtfConst cc;
   __shared__ double red[kCtfThreads / 32];
@@ -212,25 +221,25 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   if (ctf_params && threadIdx.x == 0) cc = ctf_const(ctf_params + 8 * b, d, apix);
   float2 *zb = Z + (int64_t)b * d * d;
   const float rd = 1.f / (float)d;
-  // load the 16 lines
+  // load the kLines lines
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
     const int i = fdiv_small(idx, rd), y = idx - i * d;
-    a[i * ls + y] = zb[(int64_t)pass2_line(blk, i, d) * d + y];
+    a[i * ls + y] = zb[(int64_t)pass2_line<kHalf>(blk, i, d) * d + y];
   }
   __syncthreads();
   float2 *L = fft_lines(a, bb, kLines, pl, tws, ls);
-  // combine: thread per (pair i, ky); the first CTA has a ninth "pair", the
-  // self-paired line d/2 in slot 8
+  // combine: thread per (pair i, ky); the first CTA has one more "pair",
+  // the self-paired line d/2 in slot kHalf
   float lsum = 0.f;
-  const int npair = blk == 0 ? 9 : 8;
+  const int npair = blk == 0 ? kHalf + 1 : kHalf;
   for (int idx = threadIdx.x; idx < npair * d; idx += blockDim.x) {
     int i = fdiv_small(idx, rd), ky = idx - i * d;
-    int kx = i < 8 ? 8 * blk + i : hd;
+    int kx = i < kHalf ? kHalf * blk + i : hd;
     bool self = (kx == 0 || kx == hd);
     if (self && ky > hd) continue;
     int mky = ky == 0 ? 0 : d - ky;
     float2 *l1 = L + i * ls;
-    float2 *l2 = self ? l1 : L + (8 + i) * ls;
+    float2 *l2 = self ? l1 : L + (kHalf + i) * ls;
     float2 z1 = l1[ky], z2 = l2[mky];
     // X = (z1 + conj z2) / 2,  Y = (z1 - conj z2) / (2 i)
     float2 X = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
@@ -277,12 +286,13 @@ __global__ void __launch_bounds__(kCtfThreads) ctf_pass2_kernel(
   for (int idx = threadIdx.x; idx < kLines * d; idx += blockDim.x) {
     const int i = fdiv_small(idx, rd), y = idx - i * d;
     const float2 v = R2[i * ls + y];
-    zb[(int64_t)pass2_line(blk, i, d) * d + y] = make_float2(v.x, -v.y);
+    zb[(int64_t)pass2_line<kHalf>(blk, i, d) * d + y] = make_float2(v.x, -v.y);
   }
 }
 
-// pass 3: rows y0..y0+15 of W (read transposed) -> inverse FFT along x ->
+// pass 3: rows y0 .. y0 + kLines - 1 of W (read transposed) -> inverse FFT along x ->
 // I_pred = Re / d^2, dL/dI^ = Im (2 / (B d^2)) / d^2.
+template <int kLines>
 __global__ void __launch_bounds__(kCtfThreads) ctf_pass3_kernel(
     FftPlan pl, const float2 *__restrict__ tw, const float2 *__restrict__ Z, float inv_n2,
     float gscale, float *__restrict__ pred, float *__restrict__ dproj) {
@@ -338,34 +348,54 @@ __global__ void __launch_bounds__(256) loss_mean_kernel(const double *__restrict
   }
 }
 
-size_t ctf_partials(int d) { return (size_t)(d / 16); }
+size_t ctf_partials(int d) { return (size_t)(d / ctf_lines(d)); }
+
+template <int kLines>
+static cudaError_t ctf_configure_lines(int d) {
+  int smem = (int)ctf_smem(kLines, d);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(ctf_pass1_kernel<kLines>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(ctf_pass2_kernel<kLines>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(ctf_pass3_kernel<kLines>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
 
 cudaError_t ctf_configure(int d) {
-  int smem = (int)ctf_smem(d);
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(ctf_pass1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(ctf_pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(ctf_pass3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem);
+  return ctf_lines(d) == 16 ? ctf_configure_lines<16>(d) : ctf_configure_lines<8>(d);
+}
+
+template <int kLines>
+static void launch_ctf_passes(int d, int B, float apix, const FftPlan &plan, const float2 *tw,
+                              const float *proj, const float *ctf, const float *ctf_params,
+                              const float *images, float2 *Z, double *lossp, float *pred,
+                              float *dproj, cudaStream_t st) {
+  const size_t smem = ctf_smem(kLines, d);
+  const int nblk = d / kLines;
+  const float cscale = (float)(2.0 / ((double)B * d * d));
+  ctf_pass1_kernel<kLines><<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(proj, images, plan, tw,
+                                                                           Z);
+  ctf_pass2_kernel<kLines><<<dim3(nblk, B), kCtfThreads, smem, st>>>(plan, tw, ctf, ctf_params,
+                                                                     apix, Z, lossp, nblk);
+  ctf_pass3_kernel<kLines><<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(
+      plan, tw, Z, (float)(1.0 / ((double)d * d)), (float)(cscale / ((double)d * d)), pred,
+      dproj);
 }
 
 cudaError_t launch_ctf_loss(int d, int B, float apix, const FftPlan &plan, const float2 *tw,
                             const float *proj, const float *ctf, const float *ctf_params,
                             const float *images, float2 *Z, double *lossp, float *pred,
                             float *dproj, double *loss_img, double *loss, cudaStream_t st) {
-  size_t smem = ctf_smem(d);
-  int nblk = (int)ctf_partials(d);
-  float cscale = (float)(2.0 / ((double)B * d * d));
-  ctf_pass1_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(proj, images, plan, tw, Z);
-  ctf_pass2_kernel<<<dim3(nblk, B), kCtfThreads, smem, st>>>(plan, tw, ctf, ctf_params, apix, Z,
-                                                             lossp, nblk);
-  ctf_pass3_kernel<<<dim3(d / kLines, B), kCtfThreads, smem, st>>>(
-      plan, tw, Z, (float)(1.0 / ((double)d * d)), (float)(cscale / ((double)d * d)), pred,
-      dproj);
+  const int nblk = (int)ctf_partials(d);
+  if (ctf_lines(d) == 16)
+    launch_ctf_passes<16>(d, B, apix, plan, tw, proj, ctf, ctf_params, images, Z, lossp, pred,
+                          dproj, st);
+  else
+    launch_ctf_passes<8>(d, B, apix, plan, tw, proj, ctf, ctf_params, images, Z, lossp, pred,
+                         dproj, st);
   if (loss_img || loss) {
     // per-image losses land in loss_img, or after the partials when the
     // caller does not want them (lossp holds max_B * nblk + max_B doubles)
