@@ -72,13 +72,15 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
 # the sources they depend on hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "2e868df7171ce409",
+    "source_sha256_16": "4824d37f7c381af5",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
         "A5": {
-            "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first": 1532016000.0,
-            "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first": 1524705920.0,
-            "1 lane per record, 128-record warp windows": 3881282560.0,
-            "1 lane per record, 128-record warp windows, persistent longest-first": 4823263872.0,
+            "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first": 609890304.0,
+            "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first": 615712640.0,
+            "2 lanes per record, 128-record warp windows": 1737188096.0,
+            "1 lane per record, 128-record warp windows": 1792818944.0,
+            "2 lanes per record, 128-record warp windows, persistent longest-first": 2530136320.0,
+            "1 lane per record, 128-record warp windows, persistent longest-first": 2703947520.0,
         },
     },
 }

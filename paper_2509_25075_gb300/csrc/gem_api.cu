@@ -106,7 +106,7 @@ struct gem_ctx {
 // The configurations used when neither the context nor the autotuner's cache
 // names one (the fastest measured on the benchmark workloads).
 constexpr int kDefaultFwdCfg = 3;  // block-aligned, 256-record windows, persistent longest-first
-constexpr int kDefaultBwdCfg = 1;  // one lane per record
+constexpr int kDefaultBwdCfg = 3;  // one lane per record, persistent longest-first
 
 // The autotuner's choices, shared by every context of the process: keyed by
 // device, image side, batch and the bit length of M (shapes that bin alike).
