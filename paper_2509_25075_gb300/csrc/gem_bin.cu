@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kDThreads) digit_scatter_kernel(
 // ------------------------------------------------------ tile binning ----
 
 // Geometry of the region e > log2(tau) - margin of one record, in pixel
-// units: Q(dx, dy) = al dx^2 + be dx dy + ga dy^2 <= kap with al = -ca,
-// be = -cb, ga = -cc and kap = l2A - log2(tau) + margin, reduced to what the
+// units: Q(dx, dy) = al dx^2 + be dx dy + ga dy^2 <= kap with Q = |U d|^2
+// and kap = l2A - log2(tau) + margin, reduced to what the
 // block-row ranges need (computed once per record).  Row dy of the region
 // spans dx in [c(dy) - h(dy), c(dy) + h(dy)] with
 //   c(dy) = -be dy / (2 al),  h(dy) = sqrt(4 al kap - D dy^2) / (2 al),
@@ -243,14 +243,18 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 __device__ __forceinline__ RowGeo make_row_geo(const Rec &r, float l2tau) {
-  const float al = -r.a.z, be = -r.a.w, ga = -r.b.x;
+  // Q = |U d|^2: al = u11^2, be = 2 u11 u12, ga = u12^2 + u22^2, and
+  // D = 4 al ga - be^2 = (2 u11 u22)^2 without the cancellation
+  const float u11 = r.a.z, u12 = r.a.w, u22 = r.b.x;
+  const float al = u11 * u11, be = 2.f * u11 * u12, ga = fmaf(u12, u12, u22 * u22);
   const float kap = r.b.y - l2tau + kMargin;
   RowGeo G;
   G.px = r.a.x;
   G.py = r.a.y;
   G.i2a = __fdividef(0.5f, al);
-  G.sl = -be * G.i2a;
-  G.D = 4.f * al * ga - be * be;
+  G.sl = -__fdividef(u12, u11);
+  const float t = 2.f * u11 * u22;
+  G.D = t * t;
   G.k4a = 4.f * al * kap;
   const float iD = __fdividef(1.f, G.D);
   G.xext = sqrt_approx(4.f * ga * kap * iD);

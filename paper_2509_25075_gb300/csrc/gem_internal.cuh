@@ -18,27 +18,40 @@ constexpr float kMargin = 1e-3f;
 // Device status bits (mirror GEM_STATUS_* in gem.h).
 constexpr int kStatusCapacity = 1;
 
-// Per-Gaussian quantities independent of the view (48 B):
-//   p (3), Sigma (xx, xy, xz, yy, yz, zz), log2 of the amplitude constant,
-//   valid flag, padding.
+// Per-Gaussian quantities independent of the view (64 B): p (3), log2 of
+// the amplitude constant (-inf for a Gaussian that contributes nothing),
+// the rotation Rq of its unit quaternion (row-major) and its variances
+// a = s^2.  Sigma = Rq diag(a) Rq^T is never formed entry by entry: for an
+// elongated Gaussian its entries, rounded at the scale of the largest
+// variance, lose the small ones.
 struct __align__(16) GaussPrep {
   float p[3];
-  float sig[6];
   float l2k;
-  float valid;
-  float pad;
+  float rq[9];
+  float a[3];
 };
+__device__ __forceinline__ bool gp_valid(const GaussPrep &g) { return g.l2k > -INFINITY; }
+
+// c^2 = log2(e) / 2 and c: the base-2 exponent of a 2D Gaussian is
+// l2A - c^2 d^T C d = l2A - |U d|^2 with U = c chol(C).
+constexpr float kC2 = 0.72134752044448170f;
+constexpr float kC = 0.84932180028801904f;
 
 // Projected record of one (view, Gaussian), 32 B, read by the binning and
 // the rasterisers as two float4:
-//   a = (px, py, ca, cb)  centre (pixel coordinates) and exponent terms
-//   b = (cc, l2A, rx, ry) exponent term, log2 amplitude, half extents
-// The base-2 exponent of the 2D value at pixel (u, v) is
-//   e = ca dx^2 + cb dx dy + cc dy^2 + l2A,  dx = u - px, dy = v - py,
-// so value = 2^e; the pair is kept when e > log2(tau).  rx, ry bound the
-// region where e > log2(tau) - margin.  A record whose amplitude cannot
-// exceed tau has rx = ry = -1 (no tile); an invalid record also has
-// l2A = -inf and ca = cb = cc = 0.
+//   a = (px, py, u11, u12)  centre (pixel coordinates), first row of U
+//   b = (u22, l2A, rx, ry)  last entry of U, log2 amplitude, half extents
+// U is the upper-triangular factor of the exponent's quadratic form,
+// U^T U = (log2 e / 2) S^^-1.  The base-2 exponent of the 2D value at pixel
+// (u, v) is
+//   e = l2A - z1^2 - z2^2,  z1 = u11 dx + u12 dy,  z2 = u22 dy,
+//   dx = u - px, dy = v - py,
+// so value = 2^e; the pair is kept when e > log2(tau).  (z1, z2) are the
+// whitened coordinates of the pixel: for a Gaussian a hundred times longer
+// than wide they stay of order one where the entries of S^^-1 would cancel
+// to three digits.  rx, ry bound the region where e > log2(tau) - margin.
+// A record whose amplitude cannot exceed tau has rx = ry = -1 (no tile); an
+// invalid record also has l2A = -inf and u11 = u12 = u22 = 0.
 struct __align__(16) Rec {
   float4 a;
   float4 b;
@@ -50,10 +63,10 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// 1.0f when a > b, else 0.0f (false for NaN operands).
-__device__ __forceinline__ float set_gt(float a, float b) {
+// 1.0f when a < b, else 0.0f (false for NaN operands).
+__device__ __forceinline__ float set_lt(float a, float b) {
   float y;
-  asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
   return y;
 }
 
@@ -83,12 +96,19 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 struct View2D {
   float px, py;          // centre, pixel coordinates
   float sxx, sxy, syy;   // projected covariance S^, pixel^2
-  float cxx, cxy, cyy;   // conic S^^-1, 1/pixel^2
+  float u11, u12, u22;   // U^T U = (log2 e / 2) S^^-1, U upper triangular
   float l2A;             // log2 amplitude
   float depth;           // z' (Angstrom)
   bool valid;
 };
 
+// S^ = W2 diag(a) W2^T with W2 the first two rows of W = R_b Rq: a sum of
+// three rank-one terms, each entry accurate to its own size.  Its
+// determinant comes from the Cauchy-Binet formula, det S^ = sum over column
+// pairs (k, l) of a_k a_l m_kl^2, m_kl the 2x2 minors of W2: a sum of
+// positive terms, accurate where det = sxx syy - sxy^2 would cancel (an
+// elongated Gaussian seen side on).  U follows from S^ and det S^ alone:
+//   u11 = c sqrt(syy / det),  u12 = -u11 sxy / syy,  u22 = c^2 / (u11 sqrt(det)).
 __device__ __forceinline__ View2D view_project(const GaussPrep &g, const float *__restrict__ Rv,
                                                const float *__restrict__ tv, float apix, int d) {
   View2D o;
@@ -99,31 +119,34 @@ __device__ __forceinline__ View2D view_project(const GaussPrep &g, const float *
   float inv = 1.f / apix;
   o.px = fmaf(mx, inv, 0.5f * d);
   o.py = fmaf(my, inv, 0.5f * d);
-  // S^ = R2 Sigma R2^T, R2 = first two rows of R (Angstrom^2)
-  const float *s = g.sig;  // xx xy xz yy yz zz
-  float v0x = Rv[0] * s[0] + Rv[1] * s[1] + Rv[2] * s[2];
-  float v0y = Rv[0] * s[1] + Rv[1] * s[3] + Rv[2] * s[4];
-  float v0z = Rv[0] * s[2] + Rv[1] * s[4] + Rv[2] * s[5];
-  float v1x = Rv[3] * s[0] + Rv[4] * s[1] + Rv[5] * s[2];
-  float v1y = Rv[3] * s[1] + Rv[4] * s[3] + Rv[5] * s[4];
-  float v1z = Rv[3] * s[2] + Rv[4] * s[4] + Rv[5] * s[5];
-  float axx = v0x * Rv[0] + v0y * Rv[1] + v0z * Rv[2];
-  float axy = v0x * Rv[3] + v0y * Rv[4] + v0z * Rv[5];
-  float ayy = v1x * Rv[3] + v1y * Rv[4] + v1z * Rv[5];
-  float det = axx * ayy - axy * axy;  // Angstrom^4
+  const float *q = g.rq;
+  float w0[3], w1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    w0[k] = Rv[0] * q[k] + Rv[1] * q[3 + k] + Rv[2] * q[6 + k];
+    w1[k] = Rv[3] * q[k] + Rv[4] * q[3 + k] + Rv[5] * q[6 + k];
+  }
+  const float a0 = g.a[0], a1 = g.a[1], a2 = g.a[2];
+  // Angstrom^2
+  float axx = a0 * w0[0] * w0[0] + a1 * w0[1] * w0[1] + a2 * w0[2] * w0[2];
+  float axy = a0 * w0[0] * w1[0] + a1 * w0[1] * w1[1] + a2 * w0[2] * w1[2];
+  float ayy = a0 * w1[0] * w1[0] + a1 * w1[1] * w1[1] + a2 * w1[2] * w1[2];
+  const float m12 = fmaf(w0[1], w1[2], -w0[2] * w1[1]);
+  const float m20 = fmaf(w0[2], w1[0], -w0[0] * w1[2]);
+  const float m01 = fmaf(w0[0], w1[1], -w0[1] * w1[0]);
+  float det = a1 * a2 * m12 * m12 + a0 * a2 * m20 * m20 + a0 * a1 * m01 * m01;  // Angstrom^4
   float inv2 = inv * inv;
   o.sxx = axx * inv2;
   o.sxy = axy * inv2;
   o.syy = ayy * inv2;
-  float detp = o.sxx * o.syy - o.sxy * o.sxy;
-  o.valid = g.valid != 0.f && det > 0.f && detp > 0.f && isfinite(det) && isfinite(o.px) &&
-            isfinite(o.py);
-  float idet = 1.f / detp;
-  o.cxx = o.syy * idet;
-  o.cyy = o.sxx * idet;
-  o.cxy = -o.sxy * idet;
+  float detp = det * inv2 * inv2;
+  o.u11 = kC * sqrtf(o.syy / detp);
+  o.u12 = -o.u11 * (o.sxy / o.syy);
+  o.u22 = kC2 / (o.u11 * sqrtf(detp));
   o.l2A = g.l2k - 0.5f * log2f(det);
-  o.valid = o.valid && isfinite(o.l2A) && isfinite(o.cxx) && isfinite(o.cyy) && isfinite(o.cxy);
+  o.valid = gp_valid(g) && det > 0.f && detp > 0.f && o.syy > 0.f && isfinite(det) &&
+            isfinite(o.px) && isfinite(o.py) && isfinite(o.l2A) && o.u11 > 0.f &&
+            o.u22 > 0.f && isfinite(o.u11) && isfinite(o.u12) && isfinite(o.u22);
   return o;
 }
 
@@ -183,7 +206,7 @@ struct __align__(16) QueryPrep {
   float mx, my, hz;
   float l2A;
   float valid;
-  float pad;
+  float pdet;  // det of the xy block of Sigma^-1 (1/Angstrom^4), by Cauchy-Binet
 };
 cudaError_t launch_query_prep(const float *params, int64_t M, int norm_mode, int shape,
                               QueryPrep *qp, cudaStream_t st);

@@ -112,14 +112,12 @@ __global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict
   float iq = ok ? 1.f / qn : 0.f;
   float R[9];
   quat_rot(qw * iq, qx * iq, qy * iq, qz * iq, R);
-  float a0 = s0 * s0, a1 = s1 * s1, a2 = s2 * s2;
-  // Sigma = R diag(s^2) R^T
-  g.sig[0] = R[0] * R[0] * a0 + R[1] * R[1] * a1 + R[2] * R[2] * a2;
-  g.sig[1] = R[0] * R[3] * a0 + R[1] * R[4] * a1 + R[2] * R[5] * a2;
-  g.sig[2] = R[0] * R[6] * a0 + R[1] * R[7] * a1 + R[2] * R[8] * a2;
-  g.sig[3] = R[3] * R[3] * a0 + R[4] * R[4] * a1 + R[5] * R[5] * a2;
-  g.sig[4] = R[3] * R[6] * a0 + R[4] * R[7] * a1 + R[5] * R[8] * a2;
-  g.sig[5] = R[6] * R[6] * a0 + R[7] * R[7] * a1 + R[8] * R[8] * a2;
+  // Sigma = R diag(s^2) R^T, kept as its factors (see GaussPrep)
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g.rq[k] = R[k];
+  g.a[0] = s0 * s0;
+  g.a[1] = s1 * s1;
+  g.a[2] = s2 * s2;
   // amplitude constant: A = 2^l2k / sqrt(det S^ [Angstrom^4])
   //   mode 0 (Eq. render):           2^l2k = rho / (2 pi)
   //   mode 1 (line integral of G):   2^l2k = rho sqrt(2 pi) |s0 s1 s2|
@@ -128,8 +126,7 @@ __global__ void __launch_bounds__(256) gauss_prep_kernel(const float *__restrict
     g.l2k = log2f(rho / two_pi);
   else
     g.l2k = log2f(rho * sqrtf(two_pi) * fabsf(s0 * s1 * s2));
-  g.valid = (ok && isfinite(g.l2k)) ? 1.f : 0.f;
-  g.pad = 0.f;
+  if (!(ok && isfinite(g.l2k))) g.l2k = -INFINITY;
   gp[i] = g;
 }
 
@@ -166,17 +163,11 @@ __global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restr
   View2D v = view_project(g, Rl, tl, apix, d);
   Rec r;
   float kap = v.l2A - l2tau;  // exponent headroom above the threshold
-  const float ca = -0.5f * kLog2e * v.cxx, cb = -kLog2e * v.cxy, cc = -0.5f * kLog2e * v.cyy;
-  // the exponent's quadratic form as stored must stay negative definite
-  // (4 ca cc > cb^2 in float32, the test the raster backward's S^ relies on):
-  // a Gaussian so elongated that rounding breaks this counts as degenerate
-  const float q = cb * cb, ql = fmaf(cb, cb, -q);
-  const bool definite = ca < 0.f && fmaf(4.f * ca, cc, -q) - ql > 0.f;
-  if (v.valid && definite) {
-    r.a = make_float4(v.px, v.py, ca, cb);
-    r.b = make_float4(cc, v.l2A, -1.f, -1.f);
+  if (v.valid) {
+    r.a = make_float4(v.px, v.py, v.u11, v.u12);
+    r.b = make_float4(v.u22, v.l2A, -1.f, -1.f);
     if (kap > 0.f) {
-      // Q(d) = (log2 e / 2) d^T C d <= kappa + margin  =>
+      // |U d|^2 <= kappa + margin  =>
       //   |dx| <= sqrt((kappa + margin) * Sxx * 2 / log2 e), same for y
       float km = (kap + kMargin) * (2.f / kLog2e);
       r.b.z = sqrtf(km * v.sxx);
@@ -218,11 +209,13 @@ __global__ void inspect_records_kernel(const Rec *__restrict__ rec,
   const float depth = view_project(gp[sl], Rl, tl, apix, d).depth;
   float *o = out + ((int64_t)b * M + (slot_gauss ? (int64_t)slot_gauss[sl] : sl)) * 8;
   bool valid = r.b.y > -INFINITY;
+  // conic C = U^T U / c^2
+  const float u11 = r.a.z, u12 = r.a.w, u22 = r.b.x;
   o[0] = r.a.x;
   o[1] = r.a.y;
-  o[2] = r.a.z * (-2.f / kLog2e);
-  o[3] = r.a.w * (-1.f / kLog2e);
-  o[4] = r.b.x * (-2.f / kLog2e);
+  o[2] = u11 * u11 * (1.f / kC2);
+  o[3] = u11 * u12 * (1.f / kC2);
+  o[4] = fmaf(u12, u12, u22 * u22) * (1.f / kC2);
   o[5] = r.b.y;
   o[6] = depth;
   o[7] = valid ? 1.f : 0.f;
@@ -252,18 +245,21 @@ struct Kahan {
 };
 
 // Moments of one (view, Gaussian), accumulated by the raster backward over
-// the kept pixels in float64 (pixel units, dx = u - px, dy = v - py,
-// w = g * value, g = dL/dproj, S^ the projected covariance):
-//   m0 = sum w,  m1 = sum w dx,  m2 = sum w dy,
-//   N = [[m3, m4], [m4, m5]] = sum w (d d^T - S^).
-// From them (C = conic = S^^-1, pixel units):
-//   dL/dpx, dL/dpy = C (m1, m2)
-//   dL/dS^ = 1/2 C (sum w d d^T) C - 1/2 m0 C = 1/2 C N C
+// the kept pixels in float64, in the record's whitened coordinates
+// z = U d (d = (u - px, v - py) in pixels, U^T U = c^2 C, C = S^^-1 the
+// conic, c^2 = log2(e) / 2; w = g * value, g = dL/dproj):
+//   m0 = sum w,  m1 = sum w z1,  m2 = sum w z2,
+//   N = [[m3, m4], [m4, m5]] = sum w (z z^T - c^2 I).
+// Since value = A exp(-1/2 d^T C d) and C = 2 ln2 U^T U:
+//   dL/dpx, dL/dpy = sum w C d = 2 ln2 U^T (m1, m2)
+//   dL/dS^ = 1/2 C (sum w d d^T) C - 1/2 m0 C = 2 ln2^2 U^T N U
 //            (the conic's term and the amplitude's, A ~ |S^|^-1/2, already
-//             combined in N)
+//             combined in N: d d^T - S^ = U^-1 (z z^T - c^2 I) U^-T)
 //   dL/dSigma = R2^T dL/dS^ R2 / apix^2    (S^ = R2 Sigma R2^T / apix^2)
 //   dL/dp = R2^T (dL/dpx, dL/dpy) / apix
 //   dL/drho = m0 / rho;  mode 1 adds m0 / s_k to dL/ds_k.
+// For an elongated Gaussian every term here is of the size of its result;
+// the same quantities in pixel coordinates (C (sum w d d^T) C) cancel.
 // The view-independent part (Sigma -> s, q) is applied once per thread to
 // the summed dL/dSigma.
 // One thread per (slot, view group): params, gp, the moments and the
@@ -277,7 +273,7 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
   if (sl >= M) return;
   GaussPrep g = gp[sl];
   float *out = part + ((int64_t)bg * M + sl) * kNpar;
-  if (g.valid == 0.f) {
+  if (!gp_valid(g)) {
 #pragma unroll
     for (int m = 0; m < kNpar; ++m) out[m] = 0.f;
     return;
@@ -317,16 +313,16 @@ __global__ void __launch_bounds__(128) prep_bwd_kernel(
     tl[1] = __ldg(t + 2 * b + 1);
     View2D v = view_project(g, Rl, tl, apix, d);
     if (!v.valid) continue;
-    // d/dp^ (pixel units)
-    float gpx = v.cxx * m1 + v.cxy * m2;
-    float gpy = v.cxy * m1 + v.cyy * m2;
-    // dL/dS^ = 1/2 C N C (symmetric, matrix form); U = 1/2 C N
-    float nxx = 0.5f * m3, nxy = 0.5f * m4, nyy = 0.5f * m5;
-    float u_xx = v.cxx * nxx + v.cxy * nxy, u_xy = v.cxx * nxy + v.cxy * nyy;
-    float u_yx = v.cxy * nxx + v.cyy * nxy, u_yy = v.cxy * nxy + v.cyy * nyy;
-    float hxx = u_xx * v.cxx + u_xy * v.cxy;
-    float hxy = u_xx * v.cxy + u_xy * v.cyy;
-    float hyy = u_yx * v.cxy + u_yy * v.cyy;
+    // d/dp^ (pixel units) = 2 ln2 U^T (m1, m2)
+    constexpr float k2ln2 = 1.3862943611198906f, k2ln2sq = 0.96090602783640285f;  // 2 ln2, 2 ln2^2
+    const float u11 = v.u11, u12 = v.u12, u22 = v.u22;
+    float gpx = k2ln2 * (u11 * m1);
+    float gpy = k2ln2 * fmaf(u12, m1, u22 * m2);
+    // dL/dS^ = 2 ln2^2 U^T N U: P = N U (its second column), H = U^T P
+    float p01 = fmaf(m3, u12, m4 * u22), p11 = fmaf(m4, u12, m5 * u22);
+    float hxx = k2ln2sq * (u11 * u11 * m3);
+    float hxy = k2ln2sq * (u11 * p01);
+    float hyy = k2ln2sq * fmaf(u12, p01, u22 * p11);
     // dL/dSigma = R2^T H R2 / apix^2
     float i2 = inv * inv;
     float r0[3] = {Rl[0], Rl[1], Rl[2]}, r1[3] = {Rl[3], Rl[4], Rl[5]};

@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(256) query_prep_kernel(const float *__restrict
   o.pxx = R[0] * R[0] * b0 + R[1] * R[1] * b1 + R[2] * R[2] * b2;
   o.pxy = R[0] * R[3] * b0 + R[1] * R[4] * b1 + R[2] * R[5] * b2;
   o.pyy = R[3] * R[3] * b0 + R[4] * R[4] * b1 + R[5] * R[5] * b2;
+  // det of that block by Cauchy-Binet (the squared 2x2 minors of the first
+  // two rows of R, weighted): positive terms, no cancellation for an
+  // elongated Gaussian
+  const float m12 = fmaf(R[1], R[5], -R[2] * R[4]);
+  const float m20 = fmaf(R[2], R[3], -R[0] * R[5]);
+  const float m01 = fmaf(R[0], R[4], -R[1] * R[3]);
+  o.pdet = b1 * b2 * m12 * m12 + b0 * b2 * m20 * m20 + b0 * b1 * m01 * m01;
   const float sxz = R[0] * R[6] * a0 + R[1] * R[7] * a1 + R[2] * R[8] * a2;
   const float syz = R[3] * R[6] * a0 + R[4] * R[7] * a1 + R[5] * R[8] * a2;
   const float szz = R[6] * R[6] * a0 + R[7] * R[7] * a1 + R[8] * R[8] * a2;
@@ -53,6 +60,7 @@ __global__ void __launch_bounds__(256) query_prep_kernel(const float *__restrict
   const bool ok = qn > 0.f && isfinite(qn) && rho > 0.f && isfinite(rho) && isfinite(o.l2A) &&
                   isfinite(o.pxx) && isfinite(o.pxy) && isfinite(o.pyy) && isfinite(o.hz) &&
                   isfinite(o.mx) && isfinite(o.my) && isfinite(o.p[0]) && isfinite(o.p[1]) &&
+                  o.pdet > 0.f && isfinite(o.pdet) &&
                   isfinite(o.p[2]) && a0 > 0.f && a1 > 0.f && a2 > 0.f;
   o.valid = ok ? 1.f : 0.f;
   qp[j] = o;
@@ -74,11 +82,16 @@ __global__ void __launch_bounds__(256) slice_prep_kernel(const QueryPrep *__rest
   const float a2 = apix * apix;
   const float cxx = g.pxx * a2, cxy = g.pxy * a2, cyy = g.pyy * a2;  // 1/pixel^2
   const float l2A = g.l2A - 0.5f * kLog2e * dz * dz * g.hz;
-  const float det = cxx * cyy - cxy * cxy;
+  const float det = g.pdet * a2 * a2;
+  // U^T U = c^2 [[cxx, cxy], [cxy, cyy]] (the record layout of Rec)
+  const float u11 = kC * sqrtf(cxx);
+  const float u12 = u11 * (cxy / cxx);
+  const float u22 = kC2 * sqrtf(det) / u11;
   Rec r;
-  if (g.valid != 0.f && det > 0.f && isfinite(l2A)) {
-    r.a = make_float4(px, py, -0.5f * kLog2e * cxx, -kLog2e * cxy);
-    r.b = make_float4(-0.5f * kLog2e * cyy, l2A, -1.f, -1.f);
+  if (g.valid != 0.f && det > 0.f && isfinite(l2A) && u11 > 0.f && u22 > 0.f && isfinite(u11) &&
+      isfinite(u12) && isfinite(u22)) {
+    r.a = make_float4(px, py, u11, u12);
+    r.b = make_float4(u22, l2A, -1.f, -1.f);
     const float kap = l2A - l2tau;
     if (kap > 0.f) {
       const float km = (kap + kMargin) * (2.f / kLog2e);

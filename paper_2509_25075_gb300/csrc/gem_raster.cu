@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
   const int tx = t % nt, ty = t / nt;
   const int x0 = tx * kTile, y0 = ty * kTile;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float nl2tau = -l2tau;  // kept: -e < -log2(tau)
   int64_t s = tile_start[(int64_t)b * T + t];
   int64_t e = tile_start[(int64_t)b * T + t + 1];
   e = min(e, cap);
@@ -195,25 +196,26 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
         const float2 npx = f2(-A.x);
         const float2 dx01 = add2(make_float2(X0, X0 + 1.f), npx);
         const float2 dx23 = add2(make_float2(X0 + 2.f, X0 + 3.f), npx);
-        const float2 ca = f2(A.z);
-        const float2 cadx01 = mul2(ca, dx01), cadx23 = mul2(ca, dx23);
+        const float2 u11 = f2(A.z);
+        const float2 ux01 = mul2(u11, dx01), ux23 = mul2(u11, dx23);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
+          // -e = z1^2 + (z2^2 - l2A), z1 = u11 dx + u12 dy, z2 = u22 dy
           const float dy = Y0 + (float)r - A.y;
-          const float2 bdy = f2(A.w * dy);
-          const float2 cdy = f2(fmaf(Bv.x * dy, dy, Bv.y));
-          const float2 e01 = fma2(add2(cadx01, bdy), dx01, cdy);
-          const float2 e23 = fma2(add2(cadx23, bdy), dx23, cdy);
+          const float2 uy = f2(A.w * dy);
+          const float z2 = Bv.x * dy;
+          const float2 nc = f2(fmaf(z2, z2, -Bv.y));
+          const float2 z01 = add2(ux01, uy), z23 = add2(ux23, uy);
+          const float2 f01 = fma2(z01, z01, nc), f23 = fma2(z23, z23, nc);
           if (kCount) {
-            nkept += (e01.x > l2tau) + (e01.y > l2tau) + (e23.x > l2tau) + (e23.y > l2tau);
+            nkept += (f01.x < nl2tau) + (f01.y < nl2tau) + (f23.x < nl2tau) + (f23.y < nl2tau);
           } else {
             // value on kept pairs (value > tau), zero elsewhere
-            acc[2 * r] = fma2(make_float2(ex2_approx(e01.x), ex2_approx(e01.y)),
-                              make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)), acc[2 * r]);
+            acc[2 * r] = fma2(make_float2(ex2_approx(-f01.x), ex2_approx(-f01.y)),
+                              make_float2(set_lt(f01.x, nl2tau), set_lt(f01.y, nl2tau)), acc[2 * r]);
             acc[2 * r + 1] =
-                fma2(make_float2(ex2_approx(e23.x), ex2_approx(e23.y)),
-                     make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)), acc[2 * r + 1]);
+                fma2(make_float2(ex2_approx(-f23.x), ex2_approx(-f23.y)),
+                     make_float2(set_lt(f23.x, nl2tau), set_lt(f23.y, nl2tau)), acc[2 * r + 1]);
           }
         }
         if (kCount) neval += 16;
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
   __shared__ int tile_sh;
   const int nt = d / kTile, T = nt * nt;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float nl2tau = -l2tau;  // kept: -e < -log2(tau)
   const unsigned lt = (1u << lane) - 1u;
   // pixels owned across windows: two columns of one row of block ob
   const int ob = tid >> 3, ow = tid & 7;
@@ -441,25 +444,26 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
           const float2 npx = f2(-A.x);
           const float2 dx01 = add2(xs01, npx);
           const float2 dx23 = add2(xs23, npx);
-          const float2 ca = f2(A.z);
-          const float2 cadx01 = mul2(ca, dx01), cadx23 = mul2(ca, dx23);
+          const float2 u11 = f2(A.z);
+          const float2 ux01 = mul2(u11, dx01), ux23 = mul2(u11, dx23);
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            // e = (ca dx + cb dy) dx + (cc dy^2 + l2A)
+            // -e = z1^2 + (z2^2 - l2A), z1 = u11 dx + u12 dy, z2 = u22 dy
             const float dy = Y0 + (float)r - A.y;
-            const float2 bdy = f2(A.w * dy);
-            const float2 cdy = f2(fmaf(Bv.x * dy, dy, Bv.y));
-            const float2 e01 = fma2(add2(cadx01, bdy), dx01, cdy);
-            const float2 e23 = fma2(add2(cadx23, bdy), dx23, cdy);
+            const float2 uy = f2(A.w * dy);
+            const float z2 = Bv.x * dy;
+            const float2 nc = f2(fmaf(z2, z2, -Bv.y));
+            const float2 z01 = add2(ux01, uy), z23 = add2(ux23, uy);
+            const float2 f01 = fma2(z01, z01, nc), f23 = fma2(z23, z23, nc);
             if (kCount) {
-              nkept += (e01.x > l2tau) + (e01.y > l2tau) + (e23.x > l2tau) + (e23.y > l2tau);
+              nkept += (f01.x < nl2tau) + (f01.y < nl2tau) + (f23.x < nl2tau) + (f23.y < nl2tau);
             } else {
               // value on kept pairs (value > tau), zero elsewhere
-              acc[2 * r] = fma2(make_float2(ex2_approx(e01.x), ex2_approx(e01.y)),
-                                make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)), acc[2 * r]);
+              acc[2 * r] = fma2(make_float2(ex2_approx(-f01.x), ex2_approx(-f01.y)),
+                                make_float2(set_lt(f01.x, nl2tau), set_lt(f01.y, nl2tau)), acc[2 * r]);
               acc[2 * r + 1] =
-                  fma2(make_float2(ex2_approx(e23.x), ex2_approx(e23.y)),
-                       make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)), acc[2 * r + 1]);
+                  fma2(make_float2(ex2_approx(-f23.x), ex2_approx(-f23.y)),
+                       make_float2(set_lt(f23.x, nl2tau), set_lt(f23.y, nl2tau)), acc[2 * r + 1]);
             }
           }
           if (kCount) neval += 16;
@@ -633,76 +637,66 @@ cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
 }
 
 // The six moments of w = g * value over pixel rows row0 .. row0 + kRows - 1
-// of block k of the tile at (x0, y0) for one record (centre A.x, A.y and
-// exponent terms A.z, A.w, cc, l2A), added to the running totals
+// of block k of the tile at (x0, y0) for one record (centre A.x, A.y, first
+// row of U in A.z, A.w; u22, l2A), in the record's whitened coordinates
+// z1 = u11 dx + u12 dy, z2 = u22 dy, added to the running totals
 // (n0, n1), (n2, n3), (n4, n5):
-//   n0 = sum w, n1 = sum w dx, n2 = sum w dy,
-//   n3 = sum w (dx^2 - S^xx), n4 = sum w (dx dy - S^xy), n5 = sum w (dy^2 - S^yy)
-// (per row: the sums of w, w dx, w dx^2 in packed float pairs, weighted by
-// dy; the second moments taken about S^ per block).  sg is the g tile,
-// [pixel row in block][block].
+//   n0 = sum w, n1 = sum w z1, n2 = sum w z2,
+//   n3 = sum w (z1^2 - c^2), n4 = sum w z1 z2, n5 = sum w (z2^2 - c^2)
+// (per row: the sums of w, w z1, w z1^2 in packed float pairs, weighted by
+// z2, which is constant along a row; the second moments taken about c^2 I,
+// the whitened S^, per block).  sg is the g tile, [pixel row in block][block].
 template <int kRows>
 __device__ __forceinline__ void block_moments(const float4 (*__restrict__ sg)[16], int k, int x0,
-                                              int y0, int row0, const float4 &A, float cc,
-                                              float l2A, float l2tau, float sxx, float sxy,
-                                              float syy, float2 &s01, float2 &s23, float2 &s45) {
-  const float2 ca2 = f2(A.z);
-  const float cb = A.w;
-  const float fx = (float)(x0 + 4 * (k & 3)) - A.x;
-  const float fy = (float)(y0 + 4 * (k >> 2) + row0) - A.y;
-  const float2 dx01 = make_float2(fx, fx + 1.f);
-  const float2 dx23 = make_float2(fx + 2.f, fx + 3.f);
-  const float2 dxx01 = mul2(dx01, dx01), dxx23 = mul2(dx23, dx23);
-  // this block's rows: sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2
+                                              int y0, int row0, const float4 &A, float u22,
+                                              float l2A, float nl2tau, float2 &s01, float2 &s23,
+                                              float2 &s45) {
+  const float2 u11 = f2(A.z);
+  const float u12 = A.w;
+  // dx and dy rounded exactly as the forward rounds them (pixel index
+  // minus centre), so both decide Eq. accu on the same exponent
+  const float X0 = (float)(x0 + 4 * (k & 3)), Y0 = (float)(y0 + 4 * (k >> 2) + row0);
+  const float2 npx = f2(-A.x);
+  const float2 ux01 = mul2(u11, add2(make_float2(X0, X0 + 1.f), npx));
+  const float2 ux23 = mul2(u11, add2(make_float2(X0 + 2.f, X0 + 3.f), npx));
+  // this block's rows: sums of w, w z1, w z2, w z1^2, w z1 z2, w z2^2
   float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f, m5 = 0.f;
 #pragma unroll
   for (int rr = 0; rr < kRows; ++rr) {
-    const float dy = fy + (float)rr;
-    const float2 bdy = f2(cb * dy);
-    const float2 cdy = f2(fmaf(cc * dy, dy, l2A));
-    // e = (ca dx + cb dy) dx + cc dy^2 + l2A, as in the forward's terms
-    const float2 e01 = fma2(fma2(ca2, dx01, bdy), dx01, cdy);
-    const float2 e23 = fma2(fma2(ca2, dx23, bdy), dx23, cdy);
+    const float dy = Y0 + (float)rr - A.y;
+    const float2 uy = f2(u12 * dy);
+    const float z2 = u22 * dy;
+    const float2 nc = f2(fmaf(z2, z2, -l2A));
+    // -e = z1^2 + (z2^2 - l2A), as in the forward's terms
+    const float2 z01 = add2(ux01, uy), z23 = add2(ux23, uy);
+    const float2 f01 = fma2(z01, z01, nc), f23 = fma2(z23, z23, nc);
     const float4 g4 = sg[row0 + rr][k];
     // w = g * value on kept pairs (value > tau), zero elsewhere
     const float2 gm01 = mul2(make_float2(g4.x, g4.y),
-                             make_float2(set_gt(e01.x, l2tau), set_gt(e01.y, l2tau)));
+                             make_float2(set_lt(f01.x, nl2tau), set_lt(f01.y, nl2tau)));
     const float2 gm23 = mul2(make_float2(g4.z, g4.w),
-                             make_float2(set_gt(e23.x, l2tau), set_gt(e23.y, l2tau)));
-    const float2 w01 = mul2(gm01, make_float2(ex2_approx(e01.x), ex2_approx(e01.y)));
-    const float2 w23 = mul2(gm23, make_float2(ex2_approx(e23.x), ex2_approx(e23.y)));
-    // the row's sums of w, w dx and w dx^2, then weighted by dy
+                             make_float2(set_lt(f23.x, nl2tau), set_lt(f23.y, nl2tau)));
+    const float2 w01 = mul2(gm01, make_float2(ex2_approx(-f01.x), ex2_approx(-f01.y)));
+    const float2 w23 = mul2(gm23, make_float2(ex2_approx(-f23.x), ex2_approx(-f23.y)));
+    // the row's sums of w, w z1 and w z1^2, then weighted by z2
+    const float2 wz01 = mul2(w01, z01), wz23 = mul2(w23, z23);
     const float2 s0 = add2(w01, w23);
-    const float2 s1 = fma2(w23, dx23, mul2(w01, dx01));
-    const float2 s2 = fma2(w23, dxx23, mul2(w01, dxx01));
+    const float2 s1 = add2(wz01, wz23);
+    const float2 s2 = fma2(wz23, z23, mul2(wz01, z01));
     const float r0 = s0.x + s0.y, r1 = s1.x + s1.y, r2 = s2.x + s2.y;
     m0 += r0;
     m1 += r1;
     m3 += r2;
-    m2 = fmaf(r0, dy, m2);
-    m4 = fmaf(r1, dy, m4);
-    m5 = fmaf(r0 * dy, dy, m5);
+    m2 = fmaf(r0, z2, m2);
+    m4 = fmaf(r1, z2, m4);
+    m5 = fmaf(r0 * z2, z2, m5);
   }
-  // second moments about S^, then into the totals
-  m3 = fmaf(-sxx, m0, m3);
-  m4 = fmaf(-sxy, m0, m4);
-  m5 = fmaf(-syy, m0, m5);
+  // second moments about c^2 I, then into the totals
+  m3 = fmaf(-kC2, m0, m3);
+  m5 = fmaf(-kC2, m0, m5);
   s01 = add2(s01, make_float2(m0, m1));
   s23 = add2(s23, make_float2(m2, m3));
   s45 = add2(s45, make_float2(m4, m5));
-}
-
-// S^ of a record: the inverse of the conic its exponent evaluates,
-// C = -2 ln2 [[ca, cb/2], [cb/2, cc]], so S^ = log2(e) / D
-// [[-2 cc, cb], [cb, -2 ca]] with D = 4 ca cc - cb^2 (cb^2 split exactly, so
-// D keeps its digits for elongated Gaussians).
-__device__ __forceinline__ void record_cov(float ca, float cb, float cc, float &sxx, float &sxy,
-                                           float &syy) {
-  const float cb2 = cb * cb, cb2l = fmaf(cb, cb, -cb2);
-  const float rD = kLog2e / (fmaf(4.f * ca, cc, -cb2) - cb2l);
-  sxx = -2.f * cc * rD;
-  sxy = cb * rD;
-  syy = -2.f * ca * rD;
 }
 
 // kLpr lanes share one record (lane q of the group takes pixel rows
@@ -732,6 +726,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   __shared__ int tile_sh;
   const int nt = d / kTile, T = nt * nt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float nl2tau = -l2tau;  // kept: -e < -log2(tau)
   const int64_t total = tile_start[order == nullptr ? (int64_t)gridDim.y * T : (int64_t)ntiles];
   // tiles come from the grid (order == nullptr) or, in the persistent form,
   // from a shared counter over a longest-first order
@@ -827,13 +822,9 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       if (!mk) continue;  // the whole group skips: the counts are sorted
       const float4 A = sa[warp][slot];
       const float2 Bv = sb[warp][slot];
-      const float cc = Bv.x, l2A = Bv.y;
-      float sxx, sxy, syy;
-      record_cov(A.z, A.w, cc, sxx, sxy, syy);
       float2 s01 = make_float2(0.f, 0.f), s23 = s01, s45 = s01;  // lane totals: (n0, n1), (n2, n3), (n4, n5)
       for (unsigned mm = mk; mm; mm &= mm - 1)
-        block_moments<kRows>(sg, __ffs(mm) - 1, x0, y0, row0, A, cc, l2A, l2tau, sxx, sxy, syy, s01,
-                             s23, s45);
+        block_moments<kRows>(sg, __ffs(mm) - 1, x0, y0, row0, A, Bv.x, Bv.y, nl2tau, s01, s23, s45);
       float m0 = s01.x, m1 = s01.y, m2 = s23.x, m3 = s23.y, m4 = s45.x, m5 = s45.y;
 #pragma unroll
       for (int o = 1; o < kLpr; o <<= 1) {
@@ -923,14 +914,18 @@ __global__ void __launch_bounds__(256) dense_fwd_kernel(const Rec *__restrict__ 
   bool act = pix < (int64_t)d * d;
   int u = (int)(pix % d), v = (int)(pix / d);
   const Rec *rb = rec + (int64_t)b * M;
+  const float nl2tau = -l2tau;
   double acc = 0.0;
   float part = 0.f;
   for (int64_t j = 0; j < M; ++j) {
     Rec r = rb[j];
     float dx = (float)u - r.a.x, dy = (float)v - r.a.y;
-    float ee = fmaf(fmaf(r.a.z, dx, r.a.w * dy), dx, fmaf(r.b.x * dy, dy, r.b.y));
-    float val = ex2_approx(ee);
-    part += ee > l2tau ? val : 0.f;
+    // -e = z1^2 + (z2^2 - l2A), rounded as the tiled forms round it
+    float z1 = __fadd_rn(__fmul_rn(r.a.z, dx), __fmul_rn(r.a.w, dy));
+    float z2 = __fmul_rn(r.b.x, dy);
+    float ff = __fmaf_rn(z1, z1, __fmaf_rn(z2, z2, -r.b.y));
+    float val = ex2_approx(-ff);
+    part += ff < nl2tau ? val : 0.f;
     if ((j & 127) == 127) {
       acc += part;
       part = 0.f;
@@ -941,7 +936,8 @@ __global__ void __launch_bounds__(256) dense_fwd_kernel(const Rec *__restrict__ 
 }
 
 // One thread per (image, Gaussian), every pixel of the image; the same six
-// moments as the tiled backward (second moments about S^, taken per row).
+// moments as the tiled backward (whitened coordinates, second moments about
+// c^2 I, taken per row).
 __global__ void __launch_bounds__(128) dense_bwd_kernel(const Rec *__restrict__ rec, int64_t M,
                                                         int d, float l2tau,
                                                         const float *__restrict__ dproj,
@@ -951,30 +947,30 @@ __global__ void __launch_bounds__(128) dense_bwd_kernel(const Rec *__restrict__ 
   if (j >= M) return;
   Rec r = rec[(int64_t)b * M + j];
   const float *g = dproj + (int64_t)b * d * d;
+  const float nl2tau = -l2tau;
   float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const float q = r.a.w * r.a.w, ql = fmaf(r.a.w, r.a.w, -q);
-  const float rD = kLog2e / (fmaf(4.f * r.a.z, r.b.x, -q) - ql);
-  const float sxx = -2.f * r.b.x * rD, sxy = r.a.w * rD, syy = -2.f * r.a.z * rD;
   for (int v = 0; v < d; ++v) {
     float dy = (float)v - r.a.y;
-    float bdy = r.a.w * dy, cdy = fmaf(r.b.x * dy, dy, r.b.y);
+    float uy = __fmul_rn(r.a.w, dy), z2 = __fmul_rn(r.b.x, dy);
+    float nc = __fmaf_rn(z2, z2, -r.b.y);
     float r0 = 0.f, r1 = 0.f, r3 = 0.f;
     for (int u = 0; u < d; ++u) {
       float dx = (float)u - r.a.x;
-      float ee = fmaf(fmaf(r.a.z, dx, bdy), dx, cdy);
-      float val = ex2_approx(ee);
-      float gv = ee > l2tau ? __ldg(g + (int64_t)v * d + u) * val : 0.f;
+      float z1 = __fadd_rn(__fmul_rn(r.a.z, dx), uy);
+      float ff = __fmaf_rn(z1, z1, nc);
+      float val = ex2_approx(-ff);
+      float gv = ff < nl2tau ? __ldg(g + (int64_t)v * d + u) * val : 0.f;
       r0 += gv;
-      float tt = gv * dx;
+      float tt = gv * z1;
       r1 += tt;
-      r3 = fmaf(tt, dx, r3);
+      r3 = fmaf(tt, z1, r3);
     }
     m[0] += r0;
     m[1] += r1;
-    m[2] = fmaf(dy, r0, m[2]);
-    m[3] += fmaf(-sxx, r0, r3);
-    m[4] += fmaf(dy, r1, -sxy * r0);
-    m[5] = fmaf(fmaf(dy, dy, -syy), r0, m[5]);
+    m[2] = fmaf(z2, r0, m[2]);
+    m[3] += fmaf(-kC2, r0, r3);
+    m[4] = fmaf(z2, r1, m[4]);
+    m[5] = fmaf(fmaf(z2, z2, -kC2), r0, m[5]);
   }
   if (!(r.b.z >= 0.f)) {  // no region above tau: no tile, no moments
 #pragma unroll

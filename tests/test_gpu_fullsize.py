@@ -75,14 +75,20 @@ def test_fullsize_ctf_loss_sampled_images(name):
     ctx.close()
 
 
+@pytest.mark.parametrize("upstream", ["smooth", "noise"])
 @pytest.mark.parametrize("name", FULL)
-def test_fullsize_gradient_sampled_gaussians(name):
+def test_fullsize_gradient_sampled_gaussians(name, upstream):
     """The gradient of sampled Gaussians at full size, each held to the
     contract's 1e-4 of its own gradient (per entry 1e-3 where significant),
-    plus the terms of its pairs that sit within 1e-5 relative of tau."""
+    plus the terms of its pairs that sit within 1e-5 relative of tau; for a
+    smooth upstream gradient and for one that is noise (as the adjoint of a
+    loss against noisy images is)."""
     w = syn.WORKLOADS[name]
     inp = gt.inputs(w)
-    g = syn.smooth_field(w) * 1e-3
+    if upstream == "smooth":
+        g = syn.smooth_field(w) * 1e-3
+    else:
+        g = np.random.default_rng(102).normal(size=(w.B, w.d, w.d)).astype(np.float32) * 1e-3
     ctx = _ctx(w)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
     # params, R and t stay referenced: the backward reads them again
