@@ -91,6 +91,9 @@ struct gem_ctx {
   // batch of gem_query, binned for M = bins_M Gaussians, B = bins_B images
   // with threshold bins_l2tau
   bool have_bins = false;
+  // binnings so far, and the one whose longest-first tile order `order`
+  // holds (a persistent forward computed it): the backward reuses it
+  uint64_t bins_gen = 0, order_gen = ~0ull;
   bool bins_of_proj = false;
   int64_t bins_M = 0;
   int bins_B = 0;
@@ -414,6 +417,7 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   {
     StageScope sc(c, GEM_STAGE_BIN, g.zsort ? 10 : 4);
     c->have_bins = false;
+    ++c->bins_gen;
     if ((e = launch_bin(c->rec, c->bin.key, M, B, g.d, c->l2tau, g.zsort, c->bin, &perm,
                         c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "bin");
@@ -430,6 +434,7 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
                                c->bin.tile_start, c->bin.cap, M, B, g.d, c->l2tau, proj, c->order,
                                c->next_tile, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "raster_fwd");
+    if (fwd_config(fc).persistent) c->order_gen = c->bins_gen;
   }
   c->have_proj = true;
   return GEM_OK;
@@ -482,8 +487,13 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
   // the whole buffer, should an earlier pass have stopped before clearing it
   size_t mbytes = (size_t)g.max_B * g.max_M * 6 * sizeof(double);
   {
+    // the persistent forms add a tile-order launch unless the forward's
+    // order of these bins is reused (then a counter reset, no kernel)
     StageScope sc(c, GEM_STAGE_RASTER_BWD,
-                  1 + (!dense && bwd_config(active_bwd(c, c->B, c->M)).persistent ? 1 : 0));
+                  1 + (!dense && bwd_config(active_bwd(c, c->B, c->M)).persistent &&
+                               c->order_gen != c->bins_gen
+                           ? 1
+                           : 0));
     if (!dense && !c->mom_clean && (e = cudaMemsetAsync(c->mom, 0, mbytes, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "moment clear");
     c->mom_clean = false;
@@ -492,7 +502,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     else
       e = launch_raster_bwd(active_bwd(c, c->B, c->M), c->rec, c->bin.list, c->bin.lmask,
                             c->bin.tile_start, c->bin.cap, c->M, c->B, g.d, c->l2tau, dproj, c->mom,
-                            c->order, c->next_tile + 1, c->stream);
+                            c->order, c->next_tile + 1, c->order_gen == c->bins_gen, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
   }
   StageScope sc(c, GEM_STAGE_PREP_BWD, 2);
@@ -712,6 +722,7 @@ int gem_query(gem_ctx *c, const float *params, int64_t M, float tau, float *vol)
   for (int k0 = 0; k0 < g.d; k0 += g.max_B) {
     const int ns = g.d - k0 < g.max_B ? g.d - k0 : g.max_B;
     const uint32_t *perm = nullptr;
+    ++c->bins_gen;  // the slices' bins replace the projection's
     if ((e = launch_slice_prep(c->qp, M, k0, ns, g.apix, g.d, l2tau, c->rec, c->stream)) !=
             cudaSuccess ||
         (e = launch_bin(c->rec, c->bin.key, M, ns, g.d, l2tau, 0, c->bin, &perm, c->stream)) !=
@@ -935,6 +946,7 @@ int gem_autotune(gem_ctx *c, const float *params, int64_t M, int32_t B, const fl
       cudaEventRecord(e0, c->stream);
       e = launch_raster_fwd(i, c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, M,
                             B, g.d, c->l2tau, c->proj, c->order, c->next_tile, c->stream);
+      if (e == cudaSuccess && fwd_config(i).persistent) c->order_gen = c->bins_gen;
       cudaEventRecord(e1, c->stream);
       if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
         rc = cuda_fail(c, e, "autotune forward");

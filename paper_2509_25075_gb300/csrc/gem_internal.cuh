@@ -327,10 +327,13 @@ struct BwdCfg {
 };
 int bwd_config_count();
 const BwdCfg &bwd_config(int i);
+// order_ready: `order` already holds the longest-first order of these bins
+// (a persistent forward computed it); the persistent forms then only reset
+// their counter.
 cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, uint32_t *order,
-                              unsigned *next_tile, cudaStream_t st);
+                              unsigned *next_tile, bool order_ready, cudaStream_t st);
 cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
                               const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
                               int64_t M, int B, int d, float l2tau, unsigned long long *kept,

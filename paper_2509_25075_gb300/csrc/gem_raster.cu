@@ -636,6 +636,12 @@ cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
                               kept, order, next_tile, st);
 }
 
+// The g tile is stored [pixel row in block][block ^ g_swizzle(row)]: rows 2
+// and 3 have their blocks permuted by k ^ 4, so the two lanes of a record
+// in the two-lane form (rows 0 and 2, then 1 and 3 of the same block) read
+// different banks (a float4's bank group is its index mod 8).
+__device__ __forceinline__ int g_swizzle(int row) { return (row & 2) << 1; }
+
 // The six moments of w = g * value over pixel rows row0 .. row0 + kRows - 1
 // of block k of the tile at (x0, y0) for one record (centre A.x, A.y, first
 // row of U in A.z, A.w; u22, l2A), in the record's whitened coordinates
@@ -670,7 +676,7 @@ __device__ __forceinline__ void block_moments(const float4 (*__restrict__ sg)[16
     // -e = z1^2 + (z2^2 - l2A), as in the forward's terms
     const float2 z01 = add2(ux01, uy), z23 = add2(ux23, uy);
     const float2 f01 = fma2(z01, z01, nc), f23 = fma2(z23, z23, nc);
-    const float4 g4 = sg[row0 + rr][k];
+    const float4 g4 = sg[row0 + rr][k ^ g_swizzle(row0 + rr)];
     // w = g * value on kept pairs (value > tau), zero elsewhere
     const float2 gm01 = mul2(make_float2(g4.x, g4.y),
                              make_float2(set_lt(f01.x, nl2tau), set_lt(f01.y, nl2tau)));
@@ -749,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   // g tile, stored block by block
   if (threadIdx.x < kTile * kTile / 4) {
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // pixel row, 4-column group
-    sg[r & 3][4 * (r >> 2) + q] =
+    sg[r & 3][(4 * (r >> 2) + q) ^ g_swizzle(r & 3)] =
         *reinterpret_cast<const float4 *>(dproj + ((int64_t)b * d + y0 + r) * d + x0 + 4 * q);
   }
   if (threadIdx.x == 0) next_win = kWarps;
@@ -877,7 +883,7 @@ static void launch_bwd_lanes(dim3 grid, const Rec *rec, const uint32_t *list,
 cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, uint32_t *order,
-                              unsigned *next_tile, cudaStream_t st) {
+                              unsigned *next_tile, bool order_ready, cudaStream_t st) {
   if (cfg < 0 || cfg >= bwd_config_count()) return cudaErrorInvalidValue;
   const BwdCfg &c = kBwdCfgs[cfg];
   if (c.persistent && (order == nullptr || next_tile == nullptr)) return cudaErrorInvalidValue;
@@ -886,7 +892,12 @@ cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, con
   const uint32_t *ord = nullptr;
   unsigned *ctr = nullptr;
   if (c.persistent) {
-    tile_order_kernel<<<1, 1024, 0, st>>>(tile_start, ntiles, order, next_tile);
+    if (order_ready) {
+      const cudaError_t e = cudaMemsetAsync(next_tile, 0, sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+    } else {
+      tile_order_kernel<<<1, 1024, 0, st>>>(tile_start, ntiles, order, next_tile);
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
