@@ -672,18 +672,28 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   };
   // list base of a hit's tile: the tile's start plus the chunk's offset in it
   const uint32_t *coff = tcnt + ((int64_t)b * nch + c) * T;
-  auto place = [&](uint64_t h) {
+  auto list_base = [&](uint64_t h) {
+    const int t = (int)((h >> 8) & 0xffffu);
+    return tile_start[(int64_t)b * T + t] + (int64_t)coff[t];
+  };
+  auto place = [&](uint64_t h, int64_t lb) {
     const int o = (int)(h & 255u), t = (int)((h >> 8) & 0xffffu);
     const uint32_t *bw = bm + t;
     const int word = o >> 5;
     uint32_t rank = __popc(bw[word * T] & ((1u << (o & 31)) - 1u));
     for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk * T]);
-    const int64_t pos = tile_start[(int64_t)b * T + t] + coff[t] + rank;
+    const int64_t pos = lb + rank;
     if (pos < bs.cap) {
       bs.list[pos] = sj[o];
       bs.lmask[pos] = (uint16_t)(h >> 24);
     }
   };
+  // the held hits' list bases are loaded now, so that their latency passes
+  // while the bitmaps are cleared and filled
+  int64_t hbase[kHold];
+#pragma unroll
+  for (int k = 0; k < kHold; ++k)
+    hbase[k] = threadIdx.x + k * kChunkT < H ? list_base(hold[k]) : 0;
 #pragma unroll
   for (int k = 0; k < kHold; ++k)
     if (threadIdx.x + k * kChunkT < H) zero_tile(hold[k]);
@@ -696,8 +706,11 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kHold; ++k)
-    if (threadIdx.x + k * kChunkT < H) place(hold[k]);
-  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) place(hr[i]);
+    if (threadIdx.x + k * kChunkT < H) place(hold[k], hbase[k]);
+  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) {
+    const uint64_t h = hr[i];
+    place(h, list_base(h));
+  }
 }
 
 // Bitmaps (8 words per tile, word-major).

@@ -145,48 +145,55 @@ __device__ __forceinline__ uint16_t depth_key(float z, float inv_range) {
   return (uint16_t)fminf(fmaxf(k, 0.f), 65535.f);
 }
 
+// One thread per Gaussian and group of kViewGroup views: the Gaussian's
+// 64 B are read once per group, the group's views come from shared memory.
+constexpr int kViewGroup = 8;
 __global__ void __launch_bounds__(256) view_prep_kernel(const GaussPrep *__restrict__ gp,
-                                                        int64_t M, const float *__restrict__ R,
+                                                        int64_t M, int B, const float *__restrict__ R,
                                                         const float *__restrict__ t,
                                                         float apix, int d, float l2tau,
                                                         float inv_range, Rec *__restrict__ rec,
                                                         uint16_t *__restrict__ key) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
-  if (j >= M) return;
-  GaussPrep g = gp[j];
-  float Rl[9], tl[2];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Rl[i] = __ldg(R + 9 * b + i);
-  tl[0] = __ldg(t + 2 * b);
-  tl[1] = __ldg(t + 2 * b + 1);
-  View2D v = view_project(g, Rl, tl, apix, d);
-  Rec r;
-  float kap = v.l2A - l2tau;  // exponent headroom above the threshold
-  if (v.valid) {
-    r.a = make_float4(v.px, v.py, v.u11, v.u12);
-    r.b = make_float4(v.u22, v.l2A, -1.f, -1.f);
-    if (kap > 0.f) {
-      // |U d|^2 <= kappa + margin  =>
-      //   |dx| <= sqrt((kappa + margin) * Sxx * 2 / log2 e), same for y
-      float km = (kap + kMargin) * (2.f / kLog2e);
-      r.b.z = sqrtf(km * v.sxx);
-      r.b.w = sqrtf(km * v.syy);
-    }
-    // no headroom: no extent, so no tile; every per-pair test fails anyway
-  } else {
-    r.a = make_float4(v.px, v.py, 0.f, 0.f);
-    r.b = make_float4(0.f, -INFINITY, -1.f, -1.f);
+  __shared__ float sv[kViewGroup][12];  // R (9), t (2)
+  const int b0 = blockIdx.y * kViewGroup, nv = min(kViewGroup, B - b0);
+  if (threadIdx.x < kViewGroup * 11) {
+    const int v = threadIdx.x / 11, k = threadIdx.x - v * 11;
+    if (v < nv) sv[v][k] = k < 9 ? R[9 * (b0 + v) + k] : t[2 * (b0 + v) + (k - 9)];
   }
-  rec[(int64_t)b * M + j] = r;
-  key[(int64_t)b * M + j] = depth_key(v.depth, inv_range);
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const GaussPrep g = gp[j];
+  for (int vv = 0; vv < nv; ++vv) {
+    const int b = b0 + vv;
+    View2D v = view_project(g, sv[vv], sv[vv] + 9, apix, d);
+    Rec r;
+    float kap = v.l2A - l2tau;  // exponent headroom above the threshold
+    if (v.valid) {
+      r.a = make_float4(v.px, v.py, v.u11, v.u12);
+      r.b = make_float4(v.u22, v.l2A, -1.f, -1.f);
+      if (kap > 0.f) {
+        // |U d|^2 <= kappa + margin  =>
+        //   |dx| <= sqrt((kappa + margin) * Sxx * 2 / log2 e), same for y
+        float km = (kap + kMargin) * (2.f / kLog2e);
+        r.b.z = sqrtf(km * v.sxx);
+        r.b.w = sqrtf(km * v.syy);
+      }
+      // no headroom: no extent, so no tile; every per-pair test fails anyway
+    } else {
+      r.a = make_float4(v.px, v.py, 0.f, 0.f);
+      r.b = make_float4(0.f, -INFINITY, -1.f, -1.f);
+    }
+    rec[(int64_t)b * M + j] = r;
+    key[(int64_t)b * M + j] = depth_key(v.depth, inv_range);
+  }
 }
 
 cudaError_t launch_view_prep(const GaussPrep *gp, int64_t M, int B, const float *R,
                              const float *t, float apix, int d, float l2tau, float zrange,
                              Rec *rec, uint16_t *key, cudaStream_t st) {
-  dim3 grid((unsigned)((M + 255) / 256), (unsigned)B);
-  view_prep_kernel<<<grid, 256, 0, st>>>(gp, M, R, t, apix, d, l2tau, 1.f / zrange, rec, key);
+  dim3 grid((unsigned)((M + 255) / 256), (unsigned)((B + kViewGroup - 1) / kViewGroup));
+  view_prep_kernel<<<grid, 256, 0, st>>>(gp, M, B, R, t, apix, d, l2tau, 1.f / zrange, rec, key);
   return cudaGetLastError();
 }
 
