@@ -320,13 +320,23 @@ struct ChunkStage {
   unsigned short rowx[kRowCap];     // block-row column ranges (when they fit)
 };
 
+// A Gaussian whose extent box meets at most 2 x 2 tiles (most of them, for
+// Gaussians of a few pixels) is binned by its own thread: its block-row
+// ranges go straight into up to four tile masks held in registers, and it
+// takes no part in the chunk's (Gaussian, block row) and (Gaussian,
+// candidate) items.  w = 0: not such a Gaussian.
+struct SmallBox {
+  int tx0, ty0, w, by0, by1;  // first tile, tile columns (1 or 2), block rows by0..by1
+};
+
 __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict__ rec,
                                             const uint32_t *__restrict__ perm, int64_t M,
-                                            int b, int c, int d, float l2tau) {
+                                            int b, int c, int d, float l2tau, SmallBox &sbx) {
   const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
   const int64_t r = (int64_t)c * kChunkT + i;
   int ncand = 0, nrow = 0;
   unsigned packed = 0;
+  sbx.w = 0;
   if (r < M) {
     const uint32_t j = perm ? perm[(int64_t)b * M + r] : (uint32_t)r;
     const Rec rc = rec[(int64_t)b * M + j];
@@ -334,12 +344,20 @@ __device__ __forceinline__ void stage_chunk(ChunkStage &S, const Rec *__restrict
     int ulo, uhi, vlo, vhi;
     if (pixel_range(rc.a.x, rc.b.z, d, ulo, uhi) && pixel_range(rc.a.y, rc.b.w, d, vlo, vhi)) {
       const int tx0 = ulo / kTile, ty0 = vlo / kTile;
-      const int w = uhi / kTile - tx0 + 1;
-      ncand = w * (vhi / kTile - ty0 + 1);
-      nrow = (vhi >> 2) - (vlo >> 2) + 1;
-      packed = (unsigned)tx0 | ((unsigned)ty0 << 8) | ((unsigned)w << 16) |
-               ((unsigned)(vlo >> 2) << 24);
-      S.inv_w[i] = 1.f / (float)w;
+      const int w = uhi / kTile - tx0 + 1, h = vhi / kTile - ty0 + 1;
+      if (w <= 2 && h <= 2) {
+        sbx.tx0 = tx0;
+        sbx.ty0 = ty0;
+        sbx.w = w;
+        sbx.by0 = vlo >> 2;
+        sbx.by1 = vhi >> 2;
+      } else {
+        ncand = w * h;
+        nrow = (vhi >> 2) - (vlo >> 2) + 1;
+        packed = (unsigned)tx0 | ((unsigned)ty0 << 8) | ((unsigned)w << 16) |
+                 ((unsigned)(vlo >> 2) << 24);
+        S.inv_w[i] = 1.f / (float)w;
+      }
     }
   }
   S.rect[i] = packed;
@@ -449,8 +467,40 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nt = d / kTile, T = nt * nt, nb = d / 4;
   for (int i = threadIdx.x; i < T; i += blockDim.x) tc[i] = 0;
-  stage_chunk(S, rec, perm, M, b, c, d, l2tau);
+  SmallBox sbx;
+  stage_chunk(S, rec, perm, M, b, c, d, l2tau, sbx);
   const int total = S.off[kChunkT], rows = S.roff[kChunkT];
+  // this thread's own Gaussian when it meets at most 2 x 2 tiles: the masks
+  // of tiles (ty0 + a, tx0 + q) in sm[2 a + q], each row's range clipped to
+  // each tile column as candidate_mask clips it
+  unsigned sm0 = 0, sm1 = 0, sm2 = 0, sm3 = 0;
+  int nhs = 0;
+  if (sbx.w > 0) {
+    const RowGeo myg = S.geo[threadIdx.x];
+    for (int by = sbx.by0; by <= sbx.by1; ++by) {
+      const unsigned v = block_row_range(myg, by, nb);
+      const int lo = (int)(v & 255u), hi = (int)(v >> 8), sh = 4 * (by & 3);
+      const int bx0 = 4 * sbx.tx0;
+      unsigned c0 = 0, c1 = 0;
+      int l = max(lo, bx0), h = min(hi, bx0 + 3);
+      if (l <= h) c0 = ((1u << (h - l + 1)) - 1u) << (sh + l - bx0);
+      l = max(lo, bx0 + 4);
+      h = min(hi, bx0 + 7);
+      if (sbx.w > 1 && l <= h) c1 = ((1u << (h - l + 1)) - 1u) << (sh + l - bx0 - 4);
+      if ((by >> 2) == sbx.ty0) {
+        sm0 |= c0;
+        sm1 |= c1;
+      } else {
+        sm2 |= c0;
+        sm3 |= c1;
+      }
+    }
+    const int t0 = sbx.ty0 * nt + sbx.tx0;
+    if (sm0) atomicAdd(&tc[t0], 1u), ++nhs;
+    if (sm1) atomicAdd(&tc[t0 + 1], 1u), ++nhs;
+    if (sm2) atomicAdd(&tc[t0 + nt], 1u), ++nhs;
+    if (sm3) atomicAdd(&tc[t0 + nt + 1], 1u), ++nhs;
+  }
   const bool staged = rows <= kRowCap;
   if (staged) {
     // (Gaussian, block row) items spread over the threads
@@ -460,7 +510,7 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     }
     __syncthreads();
   }
-  int nh = 0;
+  int nhc = 0;
   for (int k = threadIdx.x; k < total; k += kChunkT) {
     const int o = candidate_owner(S, k, total);
     int tx, ty;
@@ -469,9 +519,10 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     if (total <= kOwnerCap) S.cmask[k] = (unsigned short)m;
     if (m) {
       atomicAdd(&tc[ty * nt + tx], 1u);
-      ++nh;
+      ++nhc;
     }
   }
+  const int nh = nhs + nhc;
   // this thread's hits go after those of lower threads
   int inc = nh;
 #pragma unroll
@@ -497,7 +548,19 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
   // the same candidates again, in the same order, with the same masks (this
   // thread's own cached ones, or computed again from the same inputs)
   int64_t dst = run_base + before;
-  for (int k = threadIdx.x; k < total && nh > 0; k += kChunkT) {
+  if (nhs > 0) {
+    const int o = threadIdx.x, t0 = sbx.ty0 * nt + sbx.tx0;
+    auto put = [&](unsigned m, int t) {
+      if (!m) return;
+      if (dst < bs.cap) bs.hits[dst] = pack_hit(o, t, m);
+      ++dst;
+    };
+    put(sm0, t0);
+    put(sm1, t0 + 1);
+    put(sm2, t0 + nt);
+    put(sm3, t0 + nt + 1);
+  }
+  for (int k = threadIdx.x; k < total && nhc > 0; k += kChunkT) {
     const unsigned mc = total <= kOwnerCap ? S.cmask[k] : 1u;
     if (!mc) continue;
     const int o = candidate_owner(S, k, total);
@@ -507,7 +570,7 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     if (!m) continue;
     if (dst < bs.cap) bs.hits[dst] = pack_hit(o, ty * nt + tx, m);
     ++dst;
-    --nh;
+    --nhc;
   }
   __syncthreads();
   uint32_t *out = tcnt + ((int64_t)b * nch + c) * T;
