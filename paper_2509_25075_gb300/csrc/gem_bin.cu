@@ -709,6 +709,13 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
   const int64_t r0 = (int64_t)c * kChunkT;
   if (r0 + threadIdx.x < M)
     sj[threadIdx.x] = perm ? perm[(int64_t)b * M + r0 + threadIdx.x] : (uint32_t)(r0 + threadIdx.x);
+  // up to 1024 tiles (d <= 512) every bitmap word is cleared at once, while
+  // the hits are still on their way; above that each hit clears its own
+  // tile's words once it has arrived
+  const bool zero_all = T <= 1024;
+  if (zero_all)
+    for (int q = 4 * threadIdx.x; q < 8 * T; q += 4 * kChunkT)
+      *reinterpret_cast<uint4 *>(bm + q) = make_uint4(0u, 0u, 0u, 0u);
   const int64_t hb = bs.chunk_base[(int64_t)b * nch + c];
   const int64_t hn = min((int64_t)bs.chunk_n[(int64_t)b * nch + c], max(bs.cap - hb, (int64_t)0));
   const int H = (int)hn;
@@ -757,10 +764,12 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
 #pragma unroll
   for (int k = 0; k < kHold; ++k)
     hbase[k] = threadIdx.x + k * kChunkT < H ? list_base(hold[k]) : 0;
+  if (!zero_all) {
 #pragma unroll
-  for (int k = 0; k < kHold; ++k)
-    if (threadIdx.x + k * kChunkT < H) zero_tile(hold[k]);
-  for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) zero_tile(hr[i]);
+    for (int k = 0; k < kHold; ++k)
+      if (threadIdx.x + k * kChunkT < H) zero_tile(hold[k]);
+    for (int i = threadIdx.x + kHold * kChunkT; i < H; i += blockDim.x) zero_tile(hr[i]);
+  }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kHold; ++k)
