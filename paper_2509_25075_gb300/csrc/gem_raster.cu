@@ -48,6 +48,21 @@ __device__ __forceinline__ float2 kahan_add(float2 s, float x) {
   const float t = s.x + y;
   return make_float2(t, (t - s.x) - y);
 }
+// The 32 x 32 bit matrix whose row r is lane r's x, transposed: lane k gets
+// the bits k of all lanes (bit r from lane r), as 32 ballots would give it.
+// Five butterfly stages; at distance j the lanes of a pair swap the j-bit
+// halves of their 2j-bit groups that lie off the diagonal.
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
+  const unsigned hi[5] = {0xffff0000u, 0xff00ff00u, 0xf0f0f0f0u, 0xccccccccu, 0xaaaaaaaau};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & hi[s]) | ((y >> j) & ~hi[s])) : ((x & ~hi[s]) | ((y << j) & hi[s]));
+  }
+  return x;
+}
+
 constexpr int kSub = 2;                // forward: records staged per thread per window
 constexpr int kWin = kThreads * kSub;  // records staged per window
 static_assert(kThreads == 128, "the forward splits items with shifts by 7");
@@ -112,16 +127,15 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
         sa[slot] = ra;
         sb[slot] = rbv;
       }
-      unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const unsigned bk = __ballot_sync(0xffffffffu, (m[u] >> k) & 1u);
-        if (lane == k) mybal = bk;
-      }
-      if (lane < 16) {
-        wcnt[u][warp][lane] = (unsigned short)__popc(mybal);
-        wbal[u][warp][lane] = mybal;
-      }
+    }
+    // which of this warp's records touch block k, both sub-windows at once:
+    // lane k < 16 gets block k of sub-window 0, lane 16 + k block k of
+    // sub-window 1 (the lanes' packed masks, transposed as a bit matrix)
+    static_assert(kSub == 2, "two 16-bit masks per lane");
+    {
+      const unsigned bal = warp_transpose32(m[0] | (m[1] << 16), lane);
+      wcnt[lane >> 4][warp][lane & 15] = (unsigned short)__popc(bal);
+      wbal[lane >> 4][warp][lane & 15] = bal;
     }
     __syncthreads();
     // every warp: block lengths, their prefix (the items of all blocks laid
@@ -355,16 +369,15 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
           sa[slot] = ra;
           sb[slot] = rbv;
         }
-        unsigned mybal = 0;  // lane k < 16: which of this warp's records touch block k
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const unsigned bk = __ballot_sync(0xffffffffu, (m[u] >> k) & 1u);
-          if (lane == k) mybal = bk;
-        }
-        if (lane < 16) {
-          wcnt[u][warp][lane] = (unsigned short)__popc(mybal);
-          wbal[u][warp][lane] = mybal;
-        }
+      }
+      // which of this warp's records touch block k, both sub-windows at once:
+      // lane k < 16 gets block k of sub-window 0, lane 16 + k block k of
+      // sub-window 1 (the lanes' packed masks, transposed as a bit matrix)
+      static_assert(kSubW == 2, "two 16-bit masks per lane");
+      {
+        const unsigned bal = warp_transpose32(m[0] | (m[1] << 16), lane);
+        wcnt[lane >> 4][warp][lane & 15] = (unsigned short)__popc(bal);
+        wbal[lane >> 4][warp][lane & 15] = bal;
       }
       __syncthreads();
       // every warp: block lengths, their prefix, where its own records go,
@@ -399,7 +412,11 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
           for (int u = 0; u < kSubW; ++u) woff[warp][u][lane] = st + wo[u];
           // non-empty blocks before this one, plus its share of the rest
           const int neb = ne - ((len > 0) ? 1 : 0);
-          tfirst[warp][lane] = neb + (N > 0 ? ((kThreads - nne) * st) / N : 0);
+          // floor(a / N) for a = (128 - nne) st < 2^19, N <= 16 kWinW: a / N is a
+          // multiple of 1 / N, so (a + 1/2) / N sits at least 1 / (2 N) from
+          // an integer, far more than the few-ulp error of the fast division
+          const float a = (float)((kThreads - nne) * st) + 0.5f;
+          tfirst[warp][lane] = neb + (N > 0 ? (int)__fdividef(a, (float)N) : 0);
         }
         if (lane == 15) {
           pstart[warp][16] = incl;
