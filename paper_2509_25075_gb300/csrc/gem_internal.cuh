@@ -70,6 +70,14 @@ __device__ __forceinline__ float set_lt(float a, float b) {
   return y;
 }
 
+// g when a < b, else +0 (also +0 for NaN operands): a compare that yields
+// an all-ones or all-zeros word, and a bitwise and.
+__device__ __forceinline__ float keep_or_zero(float g, float a, float b) {
+  unsigned m;
+  asm("set.lt.u32.f32 %0, %1, %2;" : "=r"(m) : "f"(a), "f"(b));
+  return __uint_as_float(__float_as_uint(g) & m);
+}
+
 // Packed float32 pairs (sm_100 family): each component rounds exactly like
 // the scalar operation, two components per issued instruction.
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }

@@ -694,11 +694,11 @@ __device__ __forceinline__ void block_moments(const float4 (*__restrict__ sg)[16
     const float2 z01 = add2(ux01, uy), z23 = add2(ux23, uy);
     const float2 f01 = fma2(z01, z01, nc), f23 = fma2(z23, z23, nc);
     const float4 g4 = sg[row0 + rr][k ^ g_swizzle(row0 + rr)];
-    // w = g * value on kept pairs (value > tau), zero elsewhere
-    const float2 gm01 = mul2(make_float2(g4.x, g4.y),
-                             make_float2(set_lt(f01.x, nl2tau), set_lt(f01.y, nl2tau)));
-    const float2 gm23 = mul2(make_float2(g4.z, g4.w),
-                             make_float2(set_lt(f23.x, nl2tau), set_lt(f23.y, nl2tau)));
+    // w = g * value on kept pairs (value > tau), zero elsewhere: g is masked
+    // to +0 on the integer pipe, which leaves the FMA pipe (this loop's
+    // busiest) the multiply
+    const float2 gm01 = make_float2(keep_or_zero(g4.x, f01.x, nl2tau), keep_or_zero(g4.y, f01.y, nl2tau));
+    const float2 gm23 = make_float2(keep_or_zero(g4.z, f23.x, nl2tau), keep_or_zero(g4.w, f23.y, nl2tau));
     const float2 w01 = mul2(gm01, make_float2(ex2_approx(-f01.x), ex2_approx(-f01.y)));
     const float2 w23 = mul2(gm23, make_float2(ex2_approx(-f23.x), ex2_approx(-f23.y)));
     // the row's sums of w, w z1 and w z1^2, then weighted by z2
