@@ -56,10 +56,10 @@ FP32_PER_CLK_PER_SM = 128
 # evaluated directly (the compare runs on the ALU pipe, the exponential on
 # the SFU):
 #   forward (Eq. render, Eq. accu): dx, dy (2); the exponent
-#     (ca dx + cb dy) dx + cc dy dy + log2 A (5); the accumulation (1)  -> 8
+#     log2 A - (u11 dx + u12 dy)^2 - (u22 dy)^2 (5); the accumulation (1) -> 8
 #   backward (moments of g * value): dx, dy, exponent (7); w = g * value (1);
-#     the six moments w {1, dx, dy, dx^2, dx dy, dy^2}: 3 products, 5 adds or
-#     fused adds (8)                                                     -> 16
+#     the six moments w {1, z1, z2, z1^2, z1 z2, z2^2} in the whitened
+#     coordinates z: 3 products, 5 adds or fused adds (8)               -> 16
 # The roofline's `frac` uses these counts.  Counting every FP32 operation of
 # the direct evaluation instead (the compare and the exponent's scale as
 # well: about 10 forward, 30 backward) raises the peak's denominator less and
@@ -72,15 +72,13 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
 # the sources they depend on hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "4824d37f7c381af5",
+    "source_sha256_16": "52d72dc0fa2d8703",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
         "A5": {
-            "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first": 609890304.0,
-            "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first": 615712640.0,
-            "2 lanes per record, 128-record warp windows": 1737188096.0,
-            "1 lane per record, 128-record warp windows": 1792818944.0,
-            "2 lanes per record, 128-record warp windows, persistent longest-first": 2530136320.0,
-            "1 lane per record, 128-record warp windows, persistent longest-first": 2703947520.0,
+            "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first": 592692480.0,
+            "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first": 582146560.0,
+            "1 lane per record, 128-record warp windows, persistent longest-first": 2523966976.0,
+            "2 lanes per record, 128-record warp windows, persistent longest-first": 2423994368.0,
         },
     },
 }
