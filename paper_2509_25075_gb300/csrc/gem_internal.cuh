@@ -331,6 +331,8 @@ cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, con
 // from a counter; order [B*T] and next_tile [1] are its scratch).
 struct BwdCfg {
   int lanes, per, persistent;
+  int ctas;  // persistent grid: CTAs per SM (fewer tiles in flight keep more of
+             // their records and moments in L2)
   const char *name;
 };
 int bwd_config_count();

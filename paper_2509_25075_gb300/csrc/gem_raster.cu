@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
     unsigned long long *__restrict__ kept) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kPieces = 16 + kThreads - 1;
-  __shared__ float4 sa[kWin];                         // px, py, ca, cb
-  __shared__ float2 sb[kWin];                         // cc, log2 A
+  __shared__ float4 sa[kWin];                         // px, py, u11, u12
+  __shared__ float2 sb[kWin];                         // u22, log2 A
   __shared__ unsigned char flat[16 * kWin];           // staged slot of each (block, record) item,
                                                       // blocks in order, records in list order
   __shared__ unsigned short wcnt[kSub][kWarps][16];  // per sub-window, warp, block: how many
@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
   constexpr int kWarps = kThreads / 32;
   constexpr int kWinW = kThreads * kSubW;
   using Slot = typename FlatSlot<kSubW>::T;
-  __shared__ float4 sa[kWinW];                        // px, py, ca, cb
-  __shared__ float2 sb[kWinW];                        // cc, log2 A
+  __shared__ float4 sa[kWinW];                        // px, py, u11, u12
+  __shared__ float2 sb[kWinW];                        // u22, log2 A
   __shared__ Slot flat[16 * kWinW];                   // staged slot of each (block, record) item
   __shared__ unsigned short wcnt[kSubW][kWarps][16];  // per sub-window, warp, block: how many
   __shared__ unsigned wbal[kSubW][kWarps][16];        // per sub-window, warp, block: which lanes
@@ -740,8 +740,8 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
   // lanes of a warp read one row of many different blocks, which this
   // layout spreads over the banks (two blocks eight apart share four banks)
   __shared__ float4 sg[4][16];
-  __shared__ float4 sa[kWarps][kWW];  // px, py, ca, cb
-  __shared__ float2 sb[kWarps][kWW];  // cc, log2 A
+  __shared__ float4 sa[kWarps][kWW];  // px, py, u11, u12
+  __shared__ float2 sb[kWarps][kWW];  // u22, log2 A
   __shared__ uint32_t sj[kWarps][kWW];
   __shared__ unsigned short smask[kWarps][kWW];
   __shared__ int hist[kWarps][32];
@@ -876,25 +876,32 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
 }
 
 // The backward's kernel configurations (the autotuner's search space):
-// lanes per record, records per lane per warp window, persistent grid.
+// lanes per record, records per lane per warp window, persistent grid and
+// its CTAs per SM.
 static const BwdCfg kBwdCfgs[] = {
-    {2, 4, 0, "2 lanes per record, 128-record warp windows"},
-    {1, 4, 0, "1 lane per record, 128-record warp windows"},
-    {2, 4, 1, "2 lanes per record, 128-record warp windows, persistent longest-first"},
-    {1, 4, 1, "1 lane per record, 128-record warp windows, persistent longest-first"},
+    {2, 4, 0, 0, "2 lanes per record, 128-record warp windows"},
+    {1, 4, 0, 0, "1 lane per record, 128-record warp windows"},
+    {2, 4, 1, 8, "2 lanes per record, 128-record warp windows, persistent longest-first"},
+    {1, 4, 1, 8, "1 lane per record, 128-record warp windows, persistent longest-first"},
+    {1, 2, 1, 8, "1 lane per record, 64-record warp windows, persistent longest-first"},
+    {1, 8, 1, 7, "1 lane per record, 256-record warp windows, persistent longest-first"},
+    {2, 8, 1, 7, "2 lanes per record, 256-record warp windows, persistent longest-first"},
+    {1, 4, 1, 6, "1 lane per record, 128-record warp windows, persistent longest-first, 6 CTAs/SM"},
+    {1, 8, 1, 6, "1 lane per record, 256-record warp windows, persistent longest-first, 6 CTAs/SM"},
+    {1, 8, 1, 5, "1 lane per record, 256-record warp windows, persistent longest-first, 5 CTAs/SM"},
 };
 int bwd_config_count() { return (int)(sizeof(kBwdCfgs) / sizeof(kBwdCfgs[0])); }
 const BwdCfg &bwd_config(int i) { return kBwdCfgs[i]; }
 
-template <int kLpr>
+template <int kLpr, int kPer>
 static void launch_bwd_lanes(dim3 grid, const Rec *rec, const uint32_t *list,
                              const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
                              int64_t M, int d, float l2tau, const float *dproj, double *mom,
                              const uint32_t *order, int ntiles, unsigned *next_tile,
                              cudaStream_t st) {
-  raster_bwd_kernel<kLpr, 4><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
-                                                        l2tau, dproj, mom, order, ntiles,
-                                                        next_tile);
+  raster_bwd_kernel<kLpr, kPer><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M,
+                                                           d, l2tau, dproj, mom, order, ntiles,
+                                                           next_tile);
 }
 
 cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
@@ -918,16 +925,26 @@ cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, con
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = dim3((unsigned)max(1, min(ntiles, sms * 8)), 1);
+    grid = dim3((unsigned)max(1, min(ntiles, sms * c.ctas)), 1);
     ord = order;
     ctr = next_tile;
   }
-  if (c.lanes == 2)
-    launch_bwd_lanes<2>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
-                        ntiles, ctr, st);
+  if (c.lanes == 2 && c.per == 8)
+    launch_bwd_lanes<2, 8>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                           ntiles, ctr, st);
+  else if (c.lanes == 2)
+    launch_bwd_lanes<2, 4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                           ntiles, ctr, st);
+
+  else if (c.per == 2)
+    launch_bwd_lanes<1, 2>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                           ntiles, ctr, st);
+  else if (c.per == 8)
+    launch_bwd_lanes<1, 8>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                           ntiles, ctr, st);
   else
-    launch_bwd_lanes<1>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
-                        ntiles, ctr, st);
+    launch_bwd_lanes<1, 4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+                           ntiles, ctr, st);
   return cudaGetLastError();
 }
 
