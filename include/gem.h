@@ -387,8 +387,8 @@ int gem_ctf_loss_static(int32_t d, float apix, int32_t B, const float *proj, con
  * same result (bitwise, for a given configuration; within float rounding
  * across configurations): the forward (step a3) as equal runs of items
  * across blocks or runs aligned to blocks, at 8 or 9 CTAs per SM, on a
- * per-tile grid or a persistent grid that takes tiles longest-first from a
- * counter; the backward (a5) with 1 or 2 lanes per record, on either grid,
+ * per-tile grid or a persistent grid (5 to 9 CTAs per SM) that takes tiles
+ * longest-first from a counter; the backward (a5) with 1 or 2 lanes per record, on either grid,
  * and with warp windows of 64, 128 or 256 records and 5 to 8 CTAs per SM
  * on the persistent grid.
  * Which is

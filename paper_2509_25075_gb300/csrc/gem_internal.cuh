@@ -317,6 +317,7 @@ cudaError_t bin_configure(int d);
 // minb CTAs per SM pulling tiles longest-first from a counter.
 struct FwdCfg {
   int form, sub, minb, persistent;
+  int ctas;  // persistent grid: CTAs per SM (at most minb, the kernel's bound)
   const char *name;
 };
 int fwd_config_count();

@@ -582,11 +582,14 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int64_t *__restr
 
 // The forward's kernel configurations (the autotuner's search space).
 static const FwdCfg kFwdCfgs[] = {
-    {0, 2, 9, 0, "runs, 256-record windows, 9 CTAs/SM"},
-    {1, 2, 9, 0, "aligned, 256-record windows, 9 CTAs/SM"},
-    {1, 2, 8, 0, "aligned, 256-record windows, 8 CTAs/SM"},
-    {1, 2, 9, 1, "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first"},
-    {1, 2, 8, 1, "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first"},
+    {0, 2, 9, 0, 0, "runs, 256-record windows, 9 CTAs/SM"},
+    {1, 2, 9, 0, 0, "aligned, 256-record windows, 9 CTAs/SM"},
+    {1, 2, 8, 0, 0, "aligned, 256-record windows, 8 CTAs/SM"},
+    {1, 2, 9, 1, 9, "aligned, 256-record windows, 9 CTAs/SM, persistent longest-first"},
+    {1, 2, 8, 1, 8, "aligned, 256-record windows, 8 CTAs/SM, persistent longest-first"},
+    {1, 2, 8, 1, 7, "aligned, 256-record windows, 7 CTAs/SM, persistent longest-first"},
+    {1, 2, 8, 1, 6, "aligned, 256-record windows, 6 CTAs/SM, persistent longest-first"},
+    {1, 2, 8, 1, 5, "aligned, 256-record windows, 5 CTAs/SM, persistent longest-first"},
 };
 int fwd_config_count() { return (int)(sizeof(kFwdCfgs) / sizeof(kFwdCfgs[0])); }
 const FwdCfg &fwd_config(int i) { return kFwdCfgs[i]; }
@@ -603,7 +606,7 @@ static cudaError_t launch_aligned(const FwdCfg &c, const Rec *rec, const uint32_
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = max(1, min(ntiles, sms * kMinB));
+    const int grid = max(1, min(ntiles, sms * min(c.ctas, kMinB)));
     raster_fwd_aligned_kernel<kSubW, kMinB, kCount><<<grid, kThreads, 0, st>>>(
         rec, list, lmask, tile_start, cap, M, d, l2tau, order, ntiles, next_tile, proj, kept);
   } else {

@@ -58,7 +58,8 @@ def test_every_forward_config_matches_oracle(w, fwd):
 
 def test_persistent_forward_is_bitwise_the_per_tile_forward():
     """The persistent forms run the same tile code in another order: the
-    same bits."""
+    same bits (the persistent grids of 6 and 7 CTAs per SM run the kernel
+    built for 8)."""
     w = CASES[2]
     inp = gt.inputs(w)
     names = _n_configs()[0]
@@ -75,6 +76,8 @@ def test_persistent_forward_is_bitwise_the_per_tile_forward():
     for name, img in out.items():
         if "persistent" in name:
             base = name.split(", persistent")[0]
+            if base not in out:
+                base = "aligned, 256-record windows, 8 CTAs/SM"
             np.testing.assert_array_equal(img, out[base])
 
 
