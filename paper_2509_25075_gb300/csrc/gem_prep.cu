@@ -1,8 +1,10 @@
 // Steps a1 (preprocess) and a6 (preprocess backward) of the GEM hot path.
 //
-// a1: per Gaussian, Sigma = R_q S S^T R_q^T (Eq. G, Sec. 3.2); per (view,
-//     Gaussian), the 2D Gaussian of Eq. render: centre, conic, amplitude and
-//     the extent of the region where it can exceed tau (Eq. accu).
+// a1: per Gaussian, the factors of Sigma = R_q S S^T R_q^T (Eq. G, Sec. 3.2);
+//     per (view, Gaussian), the 2D Gaussian of Eq. render: centre, the
+//     triangular factor U of its exponent's quadratic form (U^T U =
+//     log2(e)/2 S^^-1), amplitude and the extent of the region where it can
+//     exceed tau (Eq. accu).
 // a6: chain rule from the per-(view, Gaussian) moments accumulated by the
 //     raster backward to dL/d(p, s, q, rho), summed over the views.
 #include "gem_internal.cuh"

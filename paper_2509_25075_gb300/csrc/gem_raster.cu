@@ -1,39 +1,45 @@
 // Steps a3 (raster forward) and a5 (raster backward) of the GEM hot path,
 // plus the plain dense forms used as the baseline.
 //
-// Both rasterisers run one CTA of 128 threads per (image, 16x16 tile) and
-// walk the tile's list, which is in ascending depth and carries, per entry,
-// the mask of the 4x4 pixel blocks the Gaussian's region above tau meets
-// (computed once by the binning).  A Gaussian therefore costs 16 pixel
-// evaluations per block it touches, instead of 256 per tile.
+// Both rasterisers run CTAs of 128 threads over (image, 16x16 tile) work
+// items — one per tile on a per-tile grid, or taken from a counter over a
+// longest-first tile order on a persistent grid of a chosen number of CTAs
+// per SM — and walk the tile's list, which is in ascending depth and
+// carries, per entry, the mask of the 4x4 pixel blocks the Gaussian's
+// region above tau meets (computed once by the binning).  A Gaussian
+// therefore costs 16 pixel evaluations per block it touches, instead of 256
+// per tile.  Pixels are evaluated in whitened coordinates (Rec): the
+// exponent is l2A - (u11 dx + u12 dy)^2 - (u22 dy)^2.
 //
 // a3: Eq. render restricted by Eq. accu.  Records are staged 256 at a time
-//     (a window; only the 24 bytes the evaluation reads); ballots lay the window's (block, record) items out block
-//     after block, each block's records in list order.  The items are cut
-//     into 128 equal runs, one per thread, so every thread does the same
-//     amount of work whatever the blocks' list lengths.  A thread evaluates
-//     the 16 pixels of the current block for each record of its run
-//     (packed float pairs), and writes the partial sums of every block it
-//     leaves (a piece) to shared memory; at the end of the window each pixel
-//     sums the pieces of its block in thread order and joins its running sum
-//     with Kahan compensation.  The result is deterministic and follows the
-//     list's depth order run by run.
+//     (a window; only the 24 bytes the evaluation reads).  One warp bit
+//     transpose of the lanes' packed block masks gives each block's record
+//     set; the window's (block, record) items are laid out block after
+//     block, each block's records in list order, and each block gets a
+//     share of the 128 threads in proportion to its items, so a thread
+//     never leaves its block.  A thread evaluates the 16 pixels of its block
+//     for each of its items (packed float pairs) and writes one partial
+//     image of the block; at the end of the window each pixel sums its
+//     block's partials in thread order and joins its running sum with Kahan
+//     compensation.  (The equal-runs form, raster_fwd_kernel, cuts the
+//     items into 128 equal runs across blocks instead.)  The result is
+//     deterministic and follows the list's depth order run by run.
 // a5: the "efficient gradient" of Sec. 1 (iii) / Sec. 3.2: only pairs kept by
-//     Eq. accu.  Each warp takes 128-record windows of the list (the next one
-//     not yet taken), sorts the window by block count and runs it in rounds
-//     of 16 records with neighbouring counts, two lanes per record (two
-//     pixel rows of each block each): the lanes walk the record's blocks and
-//     accumulate six moments of w = g * value (per row: the sums of w, w dx,
-//     w dx^2 in packed float pairs, weighted by dy).  The second moments are
-//     taken about the record's projected covariance S^, sum w (d d^T - S^):
+//     Eq. accu.  Each warp takes windows of 64, 128 or 256 records of the
+//     list (the next one not yet taken), sorts the window by block count
+//     and runs it in rounds of records with neighbouring counts, one or two
+//     lanes per record: the lanes walk the record's blocks and accumulate
+//     six moments of w = g * value in the record's whitened coordinates
+//     (per row: the sums of w, w z1, w z1^2 in packed float pairs, weighted
+//     by z2).  The second moments are taken about the whitened S^, c^2 I:
 //     for a wide Gaussian under a smooth upstream gradient the conic and
 //     amplitude terms of dL/dS^ nearly cancel, and this form lets that
 //     cancellation happen inside an accurate sum instead of in the float32
-//     chain rule.  Each block's sums join the lane's totals; the two lanes
-//     add their halves, and the (tile, Gaussian) partial goes to float64
-//     moments in global memory (L2 atomics), so the sum over a Gaussian's
-//     tiles loses nothing to rounding.  No barrier couples
-//     the warps.  a6 turns the moments into parameter gradients.
+//     chain rule.  Each block's sums join the lane's totals, and the (tile,
+//     Gaussian) partial goes to float64 moments in global memory (L2
+//     atomics), so the sum over a Gaussian's tiles loses nothing to
+//     rounding.  No barrier couples the warps within a tile.  a6 turns the
+//     moments into parameter gradients.
 #include <type_traits>
 
 #include "gem_internal.cuh"
