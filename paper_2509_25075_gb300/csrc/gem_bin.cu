@@ -470,7 +470,29 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
   SmallBox sbx;
   stage_chunk(S, rec, perm, M, b, c, d, l2tau, sbx);
   const int total = S.off[kChunkT], rows = S.roff[kChunkT];
-  // this thread's own Gaussian when it meets at most 2 x 2 tiles: the masks
+  const bool staged = rows <= kRowCap;
+  if (staged && rows > 0) {  // (rows is the chunk's: the barrier is uniform)
+    // (Gaussian, block row) items spread over the threads
+    for (int q = threadIdx.x; q < rows; q += kChunkT) {
+      const int o = S.rowner[q];
+      S.rowx[q] = (unsigned short)block_row_range(S.geo[o], (int)(S.rect[o] >> 24) + q - S.roff[o], nb);
+    }
+    __syncthreads();
+  }
+  int nhc = 0;
+  for (int k = threadIdx.x; k < total; k += kChunkT) {
+    const int o = candidate_owner(S, k, total);
+    int tx, ty;
+    candidate_tile(S, o, k - S.off[o], tx, ty);
+    const unsigned m = candidate_mask(S, staged, o, tx, ty, nb);
+    if (total <= kOwnerCap) S.cmask[k] = (unsigned short)m;
+    if (m) {
+      atomicAdd(&tc[ty * nt + tx], 1u);
+      ++nhc;
+    }
+  }
+  // this thread's own Gaussian when it meets at most 2 x 2 tiles (after its
+  // share of the candidates, so that one barrier waits for both): the masks
   // of tiles (ty0 + a, tx0 + q) in sm[2 a + q], each row's range clipped to
   // each tile column as candidate_mask clips it
   unsigned sm0 = 0, sm1 = 0, sm2 = 0, sm3 = 0;
@@ -500,27 +522,6 @@ __global__ void __launch_bounds__(kChunkT, 6) tile_count_kernel(
     if (sm1) atomicAdd(&tc[t0 + 1], 1u), ++nhs;
     if (sm2) atomicAdd(&tc[t0 + nt], 1u), ++nhs;
     if (sm3) atomicAdd(&tc[t0 + nt + 1], 1u), ++nhs;
-  }
-  const bool staged = rows <= kRowCap;
-  if (staged) {
-    // (Gaussian, block row) items spread over the threads
-    for (int q = threadIdx.x; q < rows; q += kChunkT) {
-      const int o = S.rowner[q];
-      S.rowx[q] = (unsigned short)block_row_range(S.geo[o], (int)(S.rect[o] >> 24) + q - S.roff[o], nb);
-    }
-    __syncthreads();
-  }
-  int nhc = 0;
-  for (int k = threadIdx.x; k < total; k += kChunkT) {
-    const int o = candidate_owner(S, k, total);
-    int tx, ty;
-    candidate_tile(S, o, k - S.off[o], tx, ty);
-    const unsigned m = candidate_mask(S, staged, o, tx, ty, nb);
-    if (total <= kOwnerCap) S.cmask[k] = (unsigned short)m;
-    if (m) {
-      atomicAdd(&tc[ty * nt + tx], 1u);
-      ++nhc;
-    }
   }
   const int nh = nhs + nhc;
   // this thread's hits go after those of lower threads
