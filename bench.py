@@ -72,7 +72,7 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
 # the sources they depend on hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "76973fb68f71db2a",
+    "source_sha256_16": "dc09b31f8d74d459",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
         "A5": {
             "aligned, 256-record windows, 7 CTAs/SM, persistent longest-first": 578653184.0,

@@ -743,6 +743,8 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
     const uint32_t *__restrict__ order, int ntiles, unsigned *__restrict__ next_tile) {
   constexpr int kWarps = kThreads / 32;
   constexpr int kWW = 32 * kPer;     // records per warp window
+  constexpr int kRpr = 32 / kLpr;    // records per round
+  constexpr int kRows = 4 / kLpr;    // pixel rows of a block per lane
   // g by pixel row within a block and block: [row][block ^ g_swizzle(row)]
   // = 4 pixels (see g_swizzle)
   __shared__ float4 sg[4][16];
