@@ -1,7 +1,9 @@
 """Parity at the workloads' full sizes, in the launch configuration bench.py
-times (same context settings), on outputs the oracle can compute one by one:
-sampled projected pixels, the loss and adjoint of sampled images, and the
-gradient of sampled Gaussians for a seeded upstream gradient."""
+times (same context settings, and the rasteriser configurations the
+autotuner picks for the shape, as bench.py picks them), on outputs the
+oracle can compute one by one: sampled projected pixels, the loss and
+adjoint of sampled images, and the gradient of sampled Gaussians for a
+seeded upstream gradient."""
 import numpy as np
 import pytest
 import torch
@@ -19,6 +21,15 @@ def _ctx(w):
     return gt.context(w, zsort=1)
 
 
+def _tuned(ctx, args):
+    """The autotuner's choice for this shape, as bench.py makes it; the
+    context then runs it (no configuration named)."""
+    f, b = ctx.gem_autotune(*args, reps=2)
+    M, B = args[0].shape[0], args[1].shape[0]
+    assert ctx.gem_get_raster_config(B, M) == (f, b)
+    return f, b
+
+
 @pytest.mark.parametrize("name", FULL)
 def test_fullsize_projection_sampled_pixels(name):
     w = syn.WORKLOADS[name]
@@ -26,6 +37,7 @@ def test_fullsize_projection_sampled_pixels(name):
     ctx = _ctx(w)
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
     args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    _tuned(ctx, args)
     ctx.gem_project(*args, proj)
     assert ctx.gem_status() == 0
     rng = np.random.default_rng(100)
@@ -93,6 +105,7 @@ def test_fullsize_gradient_sampled_gaussians(name, upstream):
     proj = torch.empty(w.B, w.d, w.d, device=gt.DEV)
     # params, R and t stay referenced: the backward reads them again
     args = [gt.to_dev(inp["params"]), gt.to_dev(inp["R"]), gt.to_dev(inp["t"])]
+    _tuned(ctx, args)
     ctx.gem_project(*args, proj)
     grad = torch.empty(w.M, 11, device=gt.DEV)
     ctx.gem_project_backward(gt.to_dev(g), grad)
