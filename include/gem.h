@@ -94,7 +94,8 @@ int gem_config_default(gem_config *cfg, int32_t d, float apix, int32_t max_B, in
 /* Create a context.  cuda_stream is a cudaStream_t (NULL: the legacy default
  * stream).  Allocates all scratch on the current device: about
  * 32 B x max_B x max_M (projected records) + 48 B x max_B x max_M (moments)
- * + 4 B x max_pairs x 1 (lists) + 20 B x max_B x d^2 (images, spectra) and
+ * + 16 B x max_pairs (list entries with their block masks, and the
+ * binning's hit records) + 20 B x max_B x d^2 (images, spectra) and
  * a few small tables.  Errors: GEM_EINVAL, GEM_ENOMEM, GEM_ECUDA. */
 int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream);
 

@@ -274,7 +274,6 @@ int gem_create(gem_ctx **out, const gem_config *cfg, void *cuda_stream) {
             alloc(c, &c->bin.tcnt, (size_t)g.max_B * nchT * c->T) &&
             alloc(c, &c->bin.tile_start, (size_t)g.max_B * c->T + 1) &&
             alloc(c, &c->bin.list, (size_t)c->cfg.max_pairs) &&
-            alloc(c, &c->bin.lmask, (size_t)c->cfg.max_pairs) &&
             alloc(c, &c->bin.hits, (size_t)c->cfg.max_pairs) &&
             alloc(c, &c->bin.chunk_base, (size_t)g.max_B * nchT) &&
             alloc(c, &c->bin.chunk_n, (size_t)g.max_B * nchT) && alloc(c, &c->bin.hit_ctr, 1) &&
@@ -430,7 +429,7 @@ int gem_project(gem_ctx *c, const float *params, int64_t M, int32_t B, const flo
   {
     const int fc = active_fwd(c, B, M);
     StageScope sc(c, GEM_STAGE_RASTER_FWD, fwd_config(fc).persistent ? 2 : 1);
-    if ((e = launch_raster_fwd(fc, c->rec, c->bin.list, c->bin.lmask,
+    if ((e = launch_raster_fwd(fc, c->rec, c->bin.list,
                                c->bin.tile_start, c->bin.cap, M, B, g.d, c->l2tau, proj, c->order,
                                c->next_tile, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "raster_fwd");
@@ -500,7 +499,7 @@ static int backward_common(gem_ctx *c, const float *dproj, float *grad, bool den
     if (dense)
       e = launch_dense_bwd(c->rec, c->M, c->B, g.d, c->l2tau, dproj, c->mom, c->stream);
     else
-      e = launch_raster_bwd(active_bwd(c, c->B, c->M), c->rec, c->bin.list, c->bin.lmask,
+      e = launch_raster_bwd(active_bwd(c, c->B, c->M), c->rec, c->bin.list,
                             c->bin.tile_start, c->bin.cap, c->M, c->B, g.d, c->l2tau, dproj, c->mom,
                             c->order, c->next_tile + 1, c->order_gen == c->bins_gen, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "raster_bwd");
@@ -626,10 +625,8 @@ int gem_inspect_bins(gem_ctx *c, int64_t *tile_start, uint32_t *list, int64_t li
   // the lists of a projection hold slots: map them to Gaussian indices
   if ((e = cudaMemcpy(tile_start, c->bin.tile_start, ts, cudaMemcpyDeviceToDevice)) !=
           cudaSuccess ||
-      (e = c->bins_of_proj
-               ? launch_map_slots(c->bin.list, c->slot_gauss, n, list, c->stream)
-               : cudaMemcpyAsync(list, c->bin.list, (size_t)n * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+      (e = launch_map_slots(c->bin.list, c->bins_of_proj ? c->slot_gauss : nullptr, n, list,
+                            c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "inspect copy");
   return GEM_OK;
@@ -654,7 +651,7 @@ int gem_pair_stats(gem_ctx *c, int64_t *kept, int64_t *evaluated) {
   if ((e = cudaMemsetAsync(c->kept, 0, 2 * sizeof(unsigned long long), c->stream)) !=
           cudaSuccess ||
       (e = launch_count_kept(active_fwd(c, c->bins_B, c->bins_M), c->rec, c->bin.list,
-                             c->bin.lmask, c->bin.tile_start, c->bin.cap, c->bins_M, c->bins_B, g.d,
+                             c->bin.tile_start, c->bin.cap, c->bins_M, c->bins_B, g.d,
                              c->bins_l2tau, c->kept, c->order, c->next_tile, c->stream)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
@@ -727,7 +724,7 @@ int gem_query(gem_ctx *c, const float *params, int64_t M, float tau, float *vol)
             cudaSuccess ||
         (e = launch_bin(c->rec, c->bin.key, M, ns, g.d, l2tau, 0, c->bin, &perm, c->stream)) !=
             cudaSuccess ||
-        (e = launch_raster_fwd(active_fwd(c, ns, M), c->rec, c->bin.list, c->bin.lmask,
+        (e = launch_raster_fwd(active_fwd(c, ns, M), c->rec, c->bin.list,
                                c->bin.tile_start, c->bin.cap, M, ns, g.d, l2tau,
                                vol + (size_t)k0 * slice, c->order, c->next_tile, c->stream)) !=
             cudaSuccess)
@@ -944,7 +941,7 @@ int gem_autotune(gem_ctx *c, const float *params, int64_t M, int32_t B, const fl
     float ms = 0.f;
     for (int r = -1; r < reps; ++r) {  // r = -1: warm-up
       cudaEventRecord(e0, c->stream);
-      e = launch_raster_fwd(i, c->rec, c->bin.list, c->bin.lmask, c->bin.tile_start, c->bin.cap, M,
+      e = launch_raster_fwd(i, c->rec, c->bin.list, c->bin.tile_start, c->bin.cap, M,
                             B, g.d, c->l2tau, c->proj, c->order, c->next_tile, c->stream);
       if (e == cudaSuccess && fwd_config(i).persistent) c->order_gen = c->bins_gen;
       cudaEventRecord(e1, c->stream);

@@ -694,7 +694,8 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(int64_t *__restrict__ 
 // their tile; a hit's place in its tile's list is the tile's start, plus the
 // chunk's offset for that tile, plus the number of lower bits set (so the
 // list keeps the chunk's depth order).  Beside the Gaussian's index the
-// entry stores its 4x4-block mask.  Only the tiles the chunk hits are
+// entry stores its 4x4-block mask, both in one 8-byte word (one scattered
+// store per hit).  Only the tiles the chunk hits are
 // touched: each hit clears its own tile's bitmap words first (a chunk hits
 // a few hundred of the image's tiles at most, and large images have
 // thousands), and looks up its own tile's list base.
@@ -754,10 +755,7 @@ __global__ void __launch_bounds__(kChunkT) tile_scatter_kernel(
     uint32_t rank = __popc(bw[word * T] & ((1u << (o & 31)) - 1u));
     for (int kk = 0; kk < word; ++kk) rank += __popc(bw[kk * T]);
     const int64_t pos = lb + rank;
-    if (pos < bs.cap) {
-      bs.list[pos] = sj[o];
-      bs.lmask[pos] = (uint16_t)(h >> 24);
-    }
+    if (pos < bs.cap) bs.list[pos] = make_uint2(sj[o], (uint32_t)(h >> 24) & 0xffffu);
   };
   // the held hits' list bases are loaded now, so that their latency passes
   // while the bitmaps are cleared and filled
@@ -818,14 +816,14 @@ cudaError_t launch_sort16(const uint16_t *key, int64_t M, int B, uint32_t *dcnt,
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) map_slots_kernel(const uint32_t *__restrict__ list,
+__global__ void __launch_bounds__(256) map_slots_kernel(const uint2 *__restrict__ list,
                                                         const uint32_t *__restrict__ slot_gauss,
                                                         int64_t n, uint32_t *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = slot_gauss[list[i]];
+  if (i < n) out[i] = slot_gauss ? slot_gauss[list[i].x] : list[i].x;
 }
 
-cudaError_t launch_map_slots(const uint32_t *list, const uint32_t *slot_gauss, int64_t n,
+cudaError_t launch_map_slots(const uint2 *list, const uint32_t *slot_gauss, int64_t n,
                              uint32_t *out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   map_slots_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(list, slot_gauss, n, out);

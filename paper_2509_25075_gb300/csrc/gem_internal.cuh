@@ -284,8 +284,7 @@ struct BinScratch {
   uint32_t *dcnt;          // [B][nchD][256]
   uint32_t *tcnt;          // [B][nchT][T] per chunk: hits per tile, then offsets
   int64_t *tile_start;     // [B*T + 1]
-  uint32_t *list;          // [cap] Gaussian index per entry
-  uint16_t *lmask;         // [cap] 4x4-block mask per entry
+  uint2 *list;             // [cap] entries: x = Gaussian index, y = 4x4-block mask (16 bits)
   uint64_t *hits;          // [cap] (slot in chunk, tile, 4x4-block mask) of every hit,
                            // grouped by chunk (written by the count pass)
   int64_t *chunk_base;     // [B][nchT] where a chunk's hits start in hits[]
@@ -299,8 +298,9 @@ struct BinScratch {
 // scratch of the binning's sizes.
 cudaError_t launch_sort16(const uint16_t *key, int64_t M, int B, uint32_t *dcnt,
                           uint32_t *packed, uint32_t *perm, cudaStream_t st);
-// Maps list entries (slots) to Gaussians: out[i] = slot_gauss[list[i]].
-cudaError_t launch_map_slots(const uint32_t *list, const uint32_t *slot_gauss, int64_t n,
+// Gaussian of each list entry: out[i] = slot_gauss[list[i].x] (the entries
+// hold slots), or list[i].x when slot_gauss is NULL.
+cudaError_t launch_map_slots(const uint2 *list, const uint32_t *slot_gauss, int64_t n,
                              uint32_t *out, cudaStream_t st);
 // Returns the permutation used for binning in *perm_out (NULL: index order).
 cudaError_t launch_bin(const Rec *rec, const uint16_t *key, int64_t M, int B, int d,
@@ -323,7 +323,7 @@ struct FwdCfg {
 int fwd_config_count();
 const FwdCfg &fwd_config(int i);
 // order [B*T] and next_tile [1] are scratch of the persistent forms.
-cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint2 *list,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, float *proj, uint32_t *order, unsigned *next_tile,
                               cudaStream_t st);
@@ -341,12 +341,12 @@ const BwdCfg &bwd_config(int i);
 // order_ready: `order` already holds the longest-first order of these bins
 // (a persistent forward computed it); the persistent forms then only reset
 // their counter.
-cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint2 *list,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, uint32_t *order,
                               unsigned *next_tile, bool order_ready, cudaStream_t st);
-cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
-                              const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint2 *list,
+                              const int64_t *tile_start, int64_t cap,
                               int64_t M, int B, int d, float l2tau, unsigned long long *kept,
                               uint32_t *order, unsigned *next_tile, cudaStream_t st);
 cudaError_t launch_dense_fwd(const Rec *rec, int64_t M, int B, int d, float l2tau, float *proj,

@@ -79,8 +79,8 @@ constexpr int kFwdMinBlocks = 9;      // forward: CTAs per SM (10, with fewer re
 // (inspection only, never on the timed path).
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
-    const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
-    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    const Rec *__restrict__ rec, const uint2 *__restrict__ list,
+    const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, float *__restrict__ proj,
     unsigned long long *__restrict__ kept) {
   constexpr int kWarps = kThreads / 32;
@@ -124,12 +124,13 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) raster_fwd_kernel(
       m[u] = 0;
       // an entry whose Gaussian index is out of range (a list position left
       // unwritten when the lists overflowed their capacity) counts as empty
-      const uint32_t jj = slot < n ? list[base + slot] : 0u;
+      const uint2 ent = slot < n ? list[base + slot] : make_uint2(0u, 0u);
+      const uint32_t jj = ent.x;
       if (slot < n && jj < (uint64_t)M) {
         const Rec *rp = rb + jj;
         const float4 ra = rp->a;
         const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
-        m[u] = lmask[base + slot];
+        m[u] = ent.y & 0xffffu;
         sa[slot] = ra;
         sb[slot] = rbv;
       }
@@ -303,8 +304,8 @@ struct FlatSlot {
 
 template <int kSubW, int kMinB, bool kCount>
 __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
-    const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
-    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    const Rec *__restrict__ rec, const uint2 *__restrict__ list,
+    const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, const uint32_t *__restrict__ order, int ntiles,
     unsigned *__restrict__ next_tile, float *__restrict__ proj,
     unsigned long long *__restrict__ kept) {
@@ -366,12 +367,13 @@ __global__ void __launch_bounds__(kThreads, kMinB) raster_fwd_aligned_kernel(
         // an entry whose Gaussian index is out of range (a list position
         // left unwritten when the lists overflowed their capacity) counts as
         // empty
-        const uint32_t jj = slot < n ? list[base + slot] : 0u;
+        const uint2 ent = slot < n ? list[base + slot] : make_uint2(0u, 0u);
+        const uint32_t jj = ent.x;
         if (slot < n && jj < (uint64_t)M) {
           const Rec *rp = rb + jj;
           const float4 ra = rp->a;
           const float2 rbv = *reinterpret_cast<const float2 *>(&rp->b);
-          m[u] = lmask[base + slot];
+          m[u] = ent.y & 0xffffu;
           sa[slot] = ra;
           sb[slot] = rbv;
         }
@@ -601,8 +603,8 @@ int fwd_config_count() { return (int)(sizeof(kFwdCfgs) / sizeof(kFwdCfgs[0])); }
 const FwdCfg &fwd_config(int i) { return kFwdCfgs[i]; }
 
 template <int kSubW, int kMinB, bool kCount>
-static cudaError_t launch_aligned(const FwdCfg &c, const Rec *rec, const uint32_t *list,
-                                  const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+static cudaError_t launch_aligned(const FwdCfg &c, const Rec *rec, const uint2 *list,
+                                  const int64_t *tile_start, int64_t cap,
                                   int64_t M, int B, int d, float l2tau, float *proj,
                                   unsigned long long *kept, uint32_t *order, unsigned *next_tile,
                                   cudaStream_t st) {
@@ -614,18 +616,18 @@ static cudaError_t launch_aligned(const FwdCfg &c, const Rec *rec, const uint32_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = max(1, min(ntiles, sms * min(c.ctas, kMinB)));
     raster_fwd_aligned_kernel<kSubW, kMinB, kCount><<<grid, kThreads, 0, st>>>(
-        rec, list, lmask, tile_start, cap, M, d, l2tau, order, ntiles, next_tile, proj, kept);
+        rec, list, tile_start, cap, M, d, l2tau, order, ntiles, next_tile, proj, kept);
   } else {
     dim3 grid(nt * nt, B);
     raster_fwd_aligned_kernel<kSubW, kMinB, kCount><<<grid, kThreads, 0, st>>>(
-        rec, list, lmask, tile_start, cap, M, d, l2tau, nullptr, 0, nullptr, proj, kept);
+        rec, list, tile_start, cap, M, d, l2tau, nullptr, 0, nullptr, proj, kept);
   }
   return cudaGetLastError();
 }
 
 template <bool kCount>
-static cudaError_t launch_fwd_any(int cfg, const Rec *rec, const uint32_t *list,
-                                  const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+static cudaError_t launch_fwd_any(int cfg, const Rec *rec, const uint2 *list,
+                                  const int64_t *tile_start, int64_t cap,
                                   int64_t M, int B, int d, float l2tau, float *proj,
                                   unsigned long long *kept, uint32_t *order, unsigned *next_tile,
                                   cudaStream_t st) {
@@ -635,30 +637,30 @@ static cudaError_t launch_fwd_any(int cfg, const Rec *rec, const uint32_t *list,
   if (c.form == 0) {
     const int nt = d / kTile;
     dim3 grid(nt * nt, B);
-    raster_fwd_kernel<kCount><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M, d,
+    raster_fwd_kernel<kCount><<<grid, kThreads, 0, st>>>(rec, list, tile_start, cap, M, d,
                                                          l2tau, proj, kept);
     return cudaGetLastError();
   }
   if (c.minb == 9)
-    return launch_aligned<2, 9, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+    return launch_aligned<2, 9, kCount>(c, rec, list, tile_start, cap, M, B, d, l2tau, proj,
                                         kept, order, next_tile, st);
-  return launch_aligned<2, 8, kCount>(c, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+  return launch_aligned<2, 8, kCount>(c, rec, list, tile_start, cap, M, B, d, l2tau, proj,
                                       kept, order, next_tile, st);
 }
 
-cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+cudaError_t launch_raster_fwd(int cfg, const Rec *rec, const uint2 *list,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, float *proj, uint32_t *order, unsigned *next_tile,
                               cudaStream_t st) {
-  return launch_fwd_any<false>(cfg, rec, list, lmask, tile_start, cap, M, B, d, l2tau, proj,
+  return launch_fwd_any<false>(cfg, rec, list, tile_start, cap, M, B, d, l2tau, proj,
                                nullptr, order, next_tile, st);
 }
 
-cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint32_t *list,
-                              const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+cudaError_t launch_count_kept(int cfg, const Rec *rec, const uint2 *list,
+                              const int64_t *tile_start, int64_t cap,
                               int64_t M, int B, int d, float l2tau, unsigned long long *kept,
                               uint32_t *order, unsigned *next_tile, cudaStream_t st) {
-  return launch_fwd_any<true>(cfg, rec, list, lmask, tile_start, cap, M, B, d, l2tau, nullptr,
+  return launch_fwd_any<true>(cfg, rec, list, tile_start, cap, M, B, d, l2tau, nullptr,
                               kept, order, next_tile, st);
 }
 
@@ -737,8 +739,8 @@ __device__ __forceinline__ void block_moments(const float4 (*__restrict__ sg)[16
 // records.
 template <int kLpr, int kPer>
 __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
-    const Rec *__restrict__ rec, const uint32_t *__restrict__ list,
-    const uint16_t *__restrict__ lmask, const int64_t *__restrict__ tile_start, int64_t cap,
+    const Rec *__restrict__ rec, const uint2 *__restrict__ list,
+    const int64_t *__restrict__ tile_start, int64_t cap,
     int64_t M, int d, float l2tau, const float *__restrict__ dproj, double *__restrict__ mom,
     const uint32_t *__restrict__ order, int ntiles, unsigned *__restrict__ next_tile) {
   constexpr int kWarps = kThreads / 32;
@@ -811,10 +813,11 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       j[q] = 0;
       m[q] = 0;
       if (i < e) {
-        j[q] = list[i];
+        const uint2 ent = list[i];
+        j[q] = ent.x;
         // an out-of-range index (an entry left unwritten when the lists
         // overflowed their capacity) counts as empty
-        m[q] = j[q] < (uint64_t)M ? lmask[i] : 0u;
+        m[q] = j[q] < (uint64_t)M ? ent.y & 0xffffu : 0u;
       }
       atomicAdd(&h[__popc(m[q])], 1);
     }
@@ -902,17 +905,17 @@ int bwd_config_count() { return (int)(sizeof(kBwdCfgs) / sizeof(kBwdCfgs[0])); }
 const BwdCfg &bwd_config(int i) { return kBwdCfgs[i]; }
 
 template <int kLpr, int kPer>
-static void launch_bwd_lanes(dim3 grid, const Rec *rec, const uint32_t *list,
-                             const uint16_t *lmask, const int64_t *tile_start, int64_t cap,
+static void launch_bwd_lanes(dim3 grid, const Rec *rec, const uint2 *list,
+                             const int64_t *tile_start, int64_t cap,
                              int64_t M, int d, float l2tau, const float *dproj, double *mom,
                              const uint32_t *order, int ntiles, unsigned *next_tile,
                              cudaStream_t st) {
-  raster_bwd_kernel<kLpr, kPer><<<grid, kThreads, 0, st>>>(rec, list, lmask, tile_start, cap, M,
+  raster_bwd_kernel<kLpr, kPer><<<grid, kThreads, 0, st>>>(rec, list, tile_start, cap, M,
                                                            d, l2tau, dproj, mom, order, ntiles,
                                                            next_tile);
 }
 
-cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, const uint16_t *lmask,
+cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint2 *list,
                               const int64_t *tile_start, int64_t cap, int64_t M, int B, int d,
                               float l2tau, const float *dproj, double *mom, uint32_t *order,
                               unsigned *next_tile, bool order_ready, cudaStream_t st) {
@@ -938,20 +941,20 @@ cudaError_t launch_raster_bwd(int cfg, const Rec *rec, const uint32_t *list, con
     ctr = next_tile;
   }
   if (c.lanes == 2 && c.per == 8)
-    launch_bwd_lanes<2, 8>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+    launch_bwd_lanes<2, 8>(grid, rec, list, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                            ntiles, ctr, st);
   else if (c.lanes == 2)
-    launch_bwd_lanes<2, 4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+    launch_bwd_lanes<2, 4>(grid, rec, list, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                            ntiles, ctr, st);
 
   else if (c.per == 2)
-    launch_bwd_lanes<1, 2>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+    launch_bwd_lanes<1, 2>(grid, rec, list, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                            ntiles, ctr, st);
   else if (c.per == 8)
-    launch_bwd_lanes<1, 8>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+    launch_bwd_lanes<1, 8>(grid, rec, list, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                            ntiles, ctr, st);
   else
-    launch_bwd_lanes<1, 4>(grid, rec, list, lmask, tile_start, cap, M, d, l2tau, dproj, mom, ord,
+    launch_bwd_lanes<1, 4>(grid, rec, list, tile_start, cap, M, d, l2tau, dproj, mom, ord,
                            ntiles, ctr, st);
   return cudaGetLastError();
 }
