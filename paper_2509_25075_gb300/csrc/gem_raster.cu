@@ -813,11 +813,13 @@ __global__ void __launch_bounds__(kThreads, 8) raster_bwd_kernel(
       j[q] = 0;
       m[q] = 0;
       if (i < e) {
-        const uint2 ent = list[i];
-        j[q] = ent.x;
+        // the entry's two words read apart, the mask only for a valid index
+        // (fewer registers in flight than one 8-byte load per entry)
+        const uint32_t *ew = reinterpret_cast<const uint32_t *>(list + i);
+        j[q] = ew[0];
         // an out-of-range index (an entry left unwritten when the lists
         // overflowed their capacity) counts as empty
-        m[q] = j[q] < (uint64_t)M ? ent.y & 0xffffu : 0u;
+        m[q] = j[q] < (uint64_t)M ? ew[1] & 0xffffu : 0u;
       }
       atomicAdd(&h[__popc(m[q])], 1);
     }
