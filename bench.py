@@ -72,15 +72,15 @@ ALL_FP32_OPS_PER_KEPT_PAIR = {"raster_fwd": 10, "raster_bwd": 30}
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass each), valid while
 # the sources they depend on hash to the value they had then (null otherwise).
 CAPTURED_TRAFFIC = {
-    "source_sha256_16": "b129f2640f18ee81",
+    "source_sha256_16": "f60b6aff05b83873",
     "per_workload": {  # workload -> {configuration name: bytes per launch}
         "A5": {
-            "aligned, 256-record windows, 7 CTAs/SM, persistent longest-first": 624402176.0,
-            "aligned, 256-record windows, 6 CTAs/SM, persistent longest-first": 621420032.0,
-            "aligned, 256-record windows, 5 CTAs/SM, persistent longest-first": 609071360.0,
-            "1 lane per record, 256-record warp windows, persistent longest-first": 2371736064.0,
-            "1 lane per record, 256-record warp windows, persistent longest-first, 6 CTAs/SM": 2371394048.0,
-            "1 lane per record, 256-record warp windows, persistent longest-first, 5 CTAs/SM": 2182457600.0,
+            "aligned, 256-record windows, 7 CTAs/SM, persistent longest-first": 623250688.0,
+            "aligned, 256-record windows, 6 CTAs/SM, persistent longest-first": 620255232.0,
+            "aligned, 256-record windows, 5 CTAs/SM, persistent longest-first": 611992064.0,
+            "1 lane per record, 256-record warp windows, persistent longest-first": 2406793216.0,
+            "1 lane per record, 256-record warp windows, persistent longest-first, 6 CTAs/SM": 2377032704.0,
+            "1 lane per record, 256-record warp windows, persistent longest-first, 5 CTAs/SM": 2201309952.0,
         },
     },
 }

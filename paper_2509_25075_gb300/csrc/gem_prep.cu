@@ -422,8 +422,18 @@ __global__ void __launch_bounds__(256) grad_sum_kernel(const float *__restrict__
   if (i >= n) return;
   const int64_t j = i / kNpar, m = i - j * kNpar;
   const int64_t src = (gauss_slot ? (int64_t)gauss_slot[j] : j) * kNpar + m;
+  // the groups' partials are loaded kU at a time, all in flight together,
+  // and summed in group order
+  constexpr int kU = 4;
   Kahan acc;
-  for (int g = 0; g < nbg; ++g) acc.add(part[(int64_t)g * n + src]);
+  for (int g0 = 0; g0 < nbg; g0 += kU) {
+    float v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = g0 + u < nbg ? part[(int64_t)(g0 + u) * n + src] : 0.f;
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (g0 + u < nbg) acc.add(v[u]);
+  }
   grad[i] = acc.s;
 }
 
