@@ -34,9 +34,8 @@ def test_fft_small_quotient_is_exact():
     gives x / D exactly for 0 <= x <= 16 n and every divisor D of n (the line
     counts n / R and the spans Ns of the Stockham stages; D = n in the CTF
     and FSC passes that split a flat index over at most 16 lines), every
-    side n.  The
-    reciprocal is also taken one unit in the last place either side, so a
-    reciprocal that is not correctly rounded keeps the result."""
+    side n.  The reciprocal is also taken one unit in the last place either
+    side, so a reciprocal that is not correctly rounded keeps the result."""
     for n in _sides():
         x = np.arange(0, 16 * n + 1, dtype=np.int64)
         xf = x.astype(f32)
